@@ -1,0 +1,233 @@
+/*
+ * hqa.h -- C ABI of the GB300 HQA-MD library (libhqa.so).
+ *
+ * HQA-MD is the hybrid quantum annealing scheme of arXiv:2004.03972: a
+ * classical molecular dynamics of continuous flux variables phi_i with
+ * momenta p_i, one per Ising spin, integrated by leapfrog under annealing
+ * schedules alpha(tau), beta(tau); the time-averaged fluxes are read out as
+ * spins, the |phibar| ranking splits frozen from ambivalent spins, and the
+ * small problem on the ambivalent spins is solved exactly.
+ *
+ * Conventions
+ *  - Every call returns hqa_status; nothing throws across the ABI.
+ *  - Host pointers are only read during the call (the caller keeps them).
+ *  - "device" pointers are CUDA global-memory pointers on the device that
+ *    was current when the context was created; the caller owns them.
+ *  - Work is enqueued on the caller's `stream` (a cudaStream_t, passed as
+ *    void* so this header needs no CUDA include; NULL = legacy stream) and
+ *    runs asynchronously.  Errors found on the device (non-finite state,
+ *    bad sub-problem sizes) are latched in the context and reported by
+ *    hqa_sync().
+ *  - Arrays indexed by replica and spin use the layout [R][N] (row-major,
+ *    replica-major): element (r, i) is at r * N + i.
+ *  - Contexts are not thread-safe; use one context per host thread, or
+ *    serialise calls.
+ */
+#ifndef HQA_H
+#define HQA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HQA_OK = 0,
+    HQA_ERR_INVALID_ARG = 1,     /* null pointer, bad size or flag */
+    HQA_ERR_ASYMMETRIC = 2,      /* J_ij != J_ji */
+    HQA_ERR_NONFINITE_INPUT = 3, /* NaN/Inf in J or h */
+    HQA_ERR_OOM = 4,             /* device allocation failed */
+    HQA_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+    HQA_ERR_UNSUPPORTED = 6,     /* valid request this build does not implement */
+    HQA_ERR_NONFINITE = 7,       /* a trajectory became NaN/Inf on the device */
+    HQA_ERR_TIMEOUT = 8,         /* a bounded device-side wait expired */
+    HQA_ERR_TOO_LARGE = 9        /* size beyond a documented limit */
+} hqa_status;
+
+typedef struct hqa_ctx hqa_ctx;
+
+/* Schedule kinds. */
+enum {
+    /* Methods, "Scheduling functions for MD":
+     *   alpha(tau) = alpha_f (tau + rho1 (1 - tau) + rho2 tau (tau - 1))
+     *   beta(tau)  = beta_f  (tau + kappa1 (1 - tau) + kappa2 tau (tau - 1)) */
+    HQA_SCHED_PAPER = 0,
+    /* alpha(tau) = gamma0 (1 - tau) (a linearly vanishing transverse-field
+     * analogue; not in the paper), beta(tau) as in HQA_SCHED_PAPER. */
+    HQA_SCHED_LINEAR_GAMMA = 1,
+    /* caller tables: table_alpha[k] = alpha at tau = k dt / 2 (k = 0..2S),
+     * table_beta[m] = beta at tau = m dt (m = 0..S). */
+    HQA_SCHED_TABLE = 2
+};
+
+/* Annealing schedule and run constants (Methods; Results Eqs. (3)-(5)). */
+typedef struct {
+    int32_t kind;                 /* HQA_SCHED_* */
+    double alpha_f, rho1, rho2;   /* paper: 0.008, 4, 3 */
+    double beta_f, kappa1, kappa2;/* paper: 0.12, 0.05, 1 */
+    double gamma0;                /* HQA_SCHED_LINEAR_GAMMA only; default 0.032 = alpha(0) */
+    int32_t M;                    /* V(phi) = phi^M, even, 2..12; paper: 6 */
+    double hstep;                 /* h = dtau / g multiplying each kick and drift; paper: 1 */
+    int32_t window;               /* W: phibar averages phi^(m), m = S-W+1..S; paper: 100 */
+    int32_t n_ambivalent;         /* n: the n smallest |phibar| are ambivalent */
+    const double* table_alpha;    /* host, HQA_SCHED_TABLE only, 2*steps+1 values */
+    const double* table_beta;     /* host, HQA_SCHED_TABLE only, steps+1 values */
+} hqa_schedule;
+
+/* Initial conditions. */
+enum {
+    HQA_INIT_PAPER = 0,       /* phi_i(0) = 0, p_i(0) = +-1 (Results, after Eq. (4)) */
+    HQA_INIT_RANDOM_FLUX = 1, /* phi_i(0) uniform on [-1/8, 1/8), p_i(0) = +-1 */
+    HQA_INIT_GIVEN = 2        /* phi0 / p0 supplied by the caller */
+};
+
+/* Arithmetic of the local-field operand. */
+enum {
+    HQA_PREC_FP32 = 0, /* phi operand FP32, FP32 accumulate */
+    HQA_PREC_BF16 = 1  /* phi operand rounded to BF16, FP32 accumulate; phi, p stay FP32 */
+};
+
+typedef struct {
+    int32_t precision;          /* HQA_PREC_*; default FP32 */
+    int32_t init;               /* HQA_INIT_*; default PAPER */
+    const float* phi0;          /* device [R][N]; HQA_INIT_GIVEN only */
+    const float* p0;            /* device [R][N]; HQA_INIT_GIVEN only */
+    int32_t replicas_per_block; /* 0 = chosen by the library; else 1,2,4,8,16,32 */
+} hqa_run_opts;
+
+/* Caller-owned device outputs of hqa_run ([R][N] unless noted).  Any
+ * pointer may be NULL to skip that output, except that spins/frozen/tally
+ * need the readout and energy/cut need spins internally (the library then
+ * uses its own workspace). */
+typedef struct {
+    float* phi;      /* phi^(S) */
+    float* p;        /* p^(S - 1/2) (leapfrog momenta are staggered) */
+    float* phibar;   /* window mean of phi (Eq. (5)) */
+    int8_t* spins;   /* s_i = sgn(phibar_i), sgn(0) = +1 */
+    uint8_t* frozen; /* 1 = frozen, 0 = ambivalent */
+    int64_t* energy; /* [R] H_Ising(s), Eq. (1); integer couplings only */
+    int64_t* cut;    /* [R] C(s) = 1/2 sum_{i<j, J_ij != 0} J_ij (1 - s_i s_j); integer couplings, h = 0 */
+    int32_t* tally;  /* [R][2] (frozen count, ambivalent count) */
+} hqa_result;
+
+/* Fills `s` with the paper's constants (Methods): alpha_f = 0.008, rho1 = 4,
+ * rho2 = 3, beta_f = 0.12, kappa1 = 0.05, kappa2 = 1, M = 6, hstep = 1,
+ * window = 100 (delta = 100 dtau, Results "Sorting ..."), n_ambivalent = 0,
+ * gamma0 = 0.032, kind = HQA_SCHED_PAPER. */
+void hqa_schedule_default(hqa_schedule* s);
+
+/* Fills `o` with defaults: FP32, HQA_INIT_PAPER, library-chosen blocking. */
+void hqa_run_opts_default(hqa_run_opts* o);
+
+/* Creates a context from dense couplings (Results Eq. (1)).
+ *   N      number of spins, 1..65536
+ *   J      host, N*N row-major float; must be symmetric; the diagonal is
+ *          ignored (all sums in Eqs. (1), (3) run over j != i)
+ *   h      host, N floats, or NULL for h = 0
+ *   flags  reserved, pass 0
+ * The couplings are copied; `*out` owns device copies.
+ * Errors: INVALID_ARG (N out of range, null J/out), ASYMMETRIC,
+ * NONFINITE_INPUT, OOM, CUDA. */
+hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t flags,
+                            hqa_ctx** out);
+
+/* Creates a context from CSR couplings (host arrays).
+ *   row_ptr  N+1 int64, row_ptr[0] = 0, non-decreasing, row_ptr[N] = nnz
+ *   col      nnz int32 in [0, N); duplicates within a row are rejected
+ *   val      nnz float
+ *   h        N floats or NULL
+ * The pattern and values must be symmetric (entry (i, j) present iff
+ * (j, i) present, equal values).  Diagonal entries are dropped.
+ * Errors: as hqa_create_dense, plus INVALID_ARG for a malformed CSR. */
+hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                          const float* val, const float* h, uint32_t flags, hqa_ctx** out);
+
+/* Queries: number of spins, stored off-diagonal entries, and whether all
+ * couplings and fields are integers (the int64 energy path). */
+hqa_status hqa_ctx_info(const hqa_ctx* ctx, int32_t* N, int64_t* nnz, int32_t* integer_couplings);
+
+/* Runs the HQA-MD leapfrog (Methods, "Leapfrog algorithm") for `steps`
+ * steps on `replicas` independent replicas, then reads out spins, the
+ * frozen/ambivalent split and the integer energy and cut.
+ *   sched     schedule and constants (hqa_schedule_default for the paper's)
+ *   dt        dtau: step m evaluates the schedule at tau = m dt; the paper
+ *             uses dt = 1 / steps
+ *   steps     S >= 1: S kicks and S drifts, producing phi^(S), p^(S-1/2)
+ *   replicas  R >= 1
+ *   seed      initial momenta p_i(0) = +-1 come from SplitMix64 (Steele,
+ *             Lea, Flood 2014): z = mix64(seed + (c + 1) * 0x9E3779B97F4A7C15)
+ *             with counter c = (r << 32) | i, p = -1 if bit 63 of z is set,
+ *             else +1.  HQA_INIT_RANDOM_FLUX draws phi_i(0) from counter
+ *             c' = 2^62 | c: phi = ((z >> 40) - 2^23) * 2^-26.
+ *   opts      NULL for defaults
+ *   out       caller-owned device buffers
+ *   stream    cudaStream_t
+ * Step j (0-based) of replica r:
+ *   p   <- p - c_j h [ alpha(j dt) M phi^(M-1) + beta(j dt) (sum_k J_ik phi_k + 2 h_i |phi_i|) ]
+ *   phi <- phi + h alpha((j + 1/2) dt) p
+ * with c_0 = 1/2 (the initial half step) and c_j = 1 otherwise.
+ * Errors: INVALID_ARG, TOO_LARGE (N x replicas-per-block exceeds on-chip
+ * capacity), UNSUPPORTED, OOM, CUDA; NONFINITE is latched if a state
+ * becomes non-finite. */
+hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+                   int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
+                   const hqa_result* out, void* stream);
+
+/* Local field of the paper's kick (Methods, "Leapfrog algorithm"):
+ *   L_i = sum_{j != i} J_ij phi_j + 2 h_i |phi_i|
+ * for R replicas.  phi, L: device [R][N] float.  The sum is evaluated by
+ * the same device code as hqa_run's field, in the given precision. */
+hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
+                           int32_t precision, void* stream);
+
+/* Readout (Results, "Sorting frozen and ambivalent variables"; HQA
+ * section): s_i = sgn(phibar_i), sgn(0) = +1; spins ordered by
+ * (|phibar_i|, i) ascending, the first n are ambivalent (frozen = 0).
+ * n is clamped to [0, N].  phibar: device [R][N] float; spins [R][N] int8;
+ * frozen [R][N] uint8; tally [R][2] int32 (may be NULL). */
+hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
+                       int8_t* spins, uint8_t* frozen, int32_t* tally, void* stream);
+
+/* Integer Ising energy (Results Eq. (1)) and MAX-CUT value (Methods,
+ * "MAX-CUT and Ising spin-glass") of R spin configurations, exact in int64.
+ * spins: device [R][N] int8 (+-1); energy, cut: device [R] int64 (either
+ * may be NULL; cut ignores h).  Requires integer couplings and fields
+ * (UNSUPPORTED otherwise). */
+hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
+                      int64_t* cut, void* stream);
+
+/* Exact solution of the reduced Ising problem on the ambivalent spins (HQA
+ * section, Eqs. (6)-(7)).  For each replica the frozen spins keep their
+ * value; the ambivalent ones (frozen == 0), taken in ascending spin index
+ * a_0 < a_1 < ..., are set to the minimiser over all 2^n assignments of
+ *   H'(s) = sum_{a<b} J_ab s_a s_b + sum_a h_eff_a s_a,
+ *   h_eff_a = h_a + sum_{k frozen} J_ak s_k,
+ * with x = sum_k [s_{a_k} = -1] 2^k and ties going to the smallest x.
+ *   spins      device [R][N] int8 (+-1)
+ *   frozen     device [R][N] uint8
+ *   n          upper bound on the ambivalent count of every replica, 0..30
+ *   out_spins  device [R][N] int8: the assembled configuration
+ *   out_energy device [R] int64: its full energy (Eq. (1)); may be NULL
+ * Requires integer couplings in {-1, 0, +1} and integer h (UNSUPPORTED
+ * otherwise); a replica with more than n ambivalent spins latches
+ * INVALID_ARG.  Uses workspace owned by the context. */
+hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                         const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                         int64_t* out_energy, void* stream);
+
+/* Waits for the context's work on `stream` and returns (and clears) the
+ * latched device-side status. */
+hqa_status hqa_sync(hqa_ctx* ctx, void* stream);
+
+/* Static description of a status code. */
+const char* hqa_status_string(hqa_status s);
+
+/* Frees the context and its device memory (synchronises the device). */
+void hqa_destroy(hqa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQA_H */

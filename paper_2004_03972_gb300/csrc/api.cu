@@ -1,0 +1,469 @@
+// api.cu -- the C ABI (include/hqa.h): argument checks, context set-up, the
+// schedule table and the stream-ordered sequence of kernels behind hqa_run.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hqa_internal.cuh"
+
+hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes)
+{
+    if (bytes <= *cap && *p) return HQA_OK;
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? HQA_ERR_OOM : HQA_ERR_CUDA;
+    }
+    *cap = want;
+    return HQA_OK;
+}
+
+namespace {
+
+void free_ctx_device(hqa_ctx* c)
+{
+    for (auto& kv : c->plans) {
+        cudaFree(kv.second.d_entries);
+        cudaFree(kv.second.d_tuples);
+        cudaFree(kv.second.d_tuple_rows);
+    }
+    c->plans.clear();
+    void* ptrs[] = {c->d_row_ptr, c->d_col,  c->d_val, c->d_val_i8, c->d_h,     c->d_h_i32,
+                    c->d_sched,   c->d_ws,   c->d_state, c->d_sub,  c->d_status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+// Builds a context from a validated symmetric CSR without diagonal or zero entries.
+hqa_status finish_create(hqa_ctx* c, hqa_ctx** out)
+{
+    HQA_CUDA_TRY(cudaGetDevice(&c->device));
+    HQA_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    int optin = 0;
+    HQA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    c->smem_optin = (size_t)optin;
+    const int N = c->N;
+    c->nnz = (int64_t)c->col.size();
+    if (c->nnz >= (int64_t)1 << 31) return HQA_ERR_TOO_LARGE;
+    // coupling classes
+    bool integer = true, unit = true;
+    int64_t sum = 0;
+    for (float v : c->val) {
+        if (v != std::nearbyint(v) || std::fabs(v) > 127.f) integer = false;
+        if (std::fabs(v) != 1.f) unit = false;
+        if (integer) sum += (int64_t)v;
+    }
+    c->has_h = false;
+    for (float v : c->h) {
+        if (v != 0.f) c->has_h = true;
+        if (v != std::nearbyint(v) || std::fabs(v) > 1048576.f) integer = false;
+    }
+    if (!c->has_h) c->h.clear();
+    c->integer = integer;
+    c->unit = unit;
+    c->sum_J_all = integer ? sum : 0;
+
+    std::vector<int32_t> rp32(N + 1);
+    for (int i = 0; i <= N; ++i) rp32[i] = (int32_t)c->row_ptr[i];
+    const size_t nz = std::max<size_t>(c->col.size(), 1);
+    HQA_CUDA_TRY(cudaMalloc(&c->d_row_ptr, (N + 1) * sizeof(int32_t)));
+    HQA_CUDA_TRY(cudaMalloc(&c->d_col, nz * sizeof(int32_t)));
+    HQA_CUDA_TRY(cudaMalloc(&c->d_val, nz * sizeof(float)));
+    HQA_CUDA_TRY(cudaMemcpy(c->d_row_ptr, rp32.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!c->col.empty()) {
+        HQA_CUDA_TRY(cudaMemcpy(c->d_col, c->col.data(), c->col.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        HQA_CUDA_TRY(cudaMemcpy(c->d_val, c->val.data(), c->val.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (integer) {
+        std::vector<int8_t> v8(nz, 0);
+        for (size_t k = 0; k < c->val.size(); ++k) v8[k] = (int8_t)c->val[k];
+        HQA_CUDA_TRY(cudaMalloc(&c->d_val_i8, nz));
+        HQA_CUDA_TRY(cudaMemcpy(c->d_val_i8, v8.data(), nz, cudaMemcpyHostToDevice));
+    }
+    if (c->has_h) {
+        HQA_CUDA_TRY(cudaMalloc(&c->d_h, N * sizeof(float)));
+        HQA_CUDA_TRY(cudaMemcpy(c->d_h, c->h.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+        if (integer) {
+            std::vector<int32_t> hi(N);
+            for (int i = 0; i < N; ++i) hi[i] = (int32_t)c->h[i];
+            HQA_CUDA_TRY(cudaMalloc(&c->d_h_i32, N * sizeof(int32_t)));
+            HQA_CUDA_TRY(cudaMemcpy(c->d_h_i32, hi.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+    }
+    HQA_CUDA_TRY(cudaMalloc(&c->d_status, sizeof(uint32_t)));
+    HQA_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+    *out = c;
+    return HQA_OK;
+}
+
+hqa_status create_guarded(hqa_ctx* c, hqa_ctx** out)
+{
+    hqa_status s = finish_create(c, out);
+    if (s != HQA_OK) {
+        free_ctx_device(c);
+        delete c;
+        *out = nullptr;
+    }
+    return s;
+}
+
+bool misaligned(const void* p, size_t a) { return p && ((uintptr_t)p % a) != 0; }
+
+bool finite_all(const float* p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+double sched_alpha(const hqa_schedule* s, double tau)
+{
+    if (s->kind == HQA_SCHED_LINEAR_GAMMA) return s->gamma0 * (1.0 - tau);
+    return s->alpha_f * (tau + s->rho1 * (1.0 - tau) + s->rho2 * tau * (tau - 1.0));
+}
+
+double sched_beta(const hqa_schedule* s, double tau)
+{
+    return s->beta_f * (tau + s->kappa1 * (1.0 - tau) + s->kappa2 * tau * (tau - 1.0));
+}
+
+hqa_status check_schedule(const hqa_schedule* s, double dt, int64_t steps)
+{
+    if (!s) return HQA_ERR_INVALID_ARG;
+    if (s->kind < HQA_SCHED_PAPER || s->kind > HQA_SCHED_TABLE) return HQA_ERR_INVALID_ARG;
+    if (s->M < 2 || s->M > 12 || (s->M & 1)) return HQA_ERR_INVALID_ARG;
+    if (!(s->hstep > 0.0) || !std::isfinite(s->hstep)) return HQA_ERR_INVALID_ARG;
+    if (s->window < 1) return HQA_ERR_INVALID_ARG;
+    if (!std::isfinite(dt) || steps < 1) return HQA_ERR_INVALID_ARG;
+    if (s->kind == HQA_SCHED_TABLE && (!s->table_alpha || !s->table_beta)) return HQA_ERR_INVALID_ARG;
+    return HQA_OK;
+}
+
+// Kick/drift coefficients per step (Methods, "Leapfrog algorithm"):
+//   kA_j = c_j h alpha(j dt) M, kB_j = c_j h beta(j dt), dA_j = h alpha((j+1/2) dt),
+// c_0 = 1/2 (initial half step), c_j = 1 after.  Computed in FP64, stored FP32.
+hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t S)
+{
+    std::vector<StepCoef> t((size_t)S);
+    for (int64_t j = 0; j < S; ++j) {
+        double a, b, ah;
+        if (s->kind == HQA_SCHED_TABLE) {
+            a = s->table_alpha[2 * j];
+            ah = s->table_alpha[2 * j + 1];
+            b = s->table_beta[j];
+        } else {
+            a = sched_alpha(s, (double)j * dt);
+            ah = sched_alpha(s, ((double)j + 0.5) * dt);
+            b = sched_beta(s, (double)j * dt);
+        }
+        if (!std::isfinite(a) || !std::isfinite(ah) || !std::isfinite(b)) return HQA_ERR_INVALID_ARG;
+        const double cj = j == 0 ? 0.5 : 1.0;
+        t[j].kA = (float)(cj * s->hstep * a * (double)s->M);
+        t[j].kB = (float)(cj * s->hstep * b);
+        t[j].dA = (float)(s->hstep * ah);
+        t[j].pad = 0.f;
+    }
+    const size_t bytes = t.size() * sizeof(StepCoef);
+    if (c->sched_host.size() == t.size() && c->d_sched &&
+        std::memcmp(c->sched_host.data(), t.data(), bytes) == 0)
+        return HQA_OK;
+    if (bytes > c->sched_cap) {
+        if (c->d_sched) cudaFree(c->d_sched);
+        c->d_sched = nullptr;
+        c->sched_cap = 0;
+        HQA_CUDA_TRY(cudaMalloc(&c->d_sched, bytes));
+        c->sched_cap = bytes;
+    }
+    // synchronous copy: the device may still read the previous table
+    HQA_CUDA_TRY(cudaDeviceSynchronize());
+    HQA_CUDA_TRY(cudaMemcpy(c->d_sched, t.data(), bytes, cudaMemcpyHostToDevice));
+    c->sched_host.swap(t);
+    return HQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hqa_schedule_default(hqa_schedule* s)
+{
+    if (!s) return;
+    std::memset(s, 0, sizeof(*s));
+    s->kind = HQA_SCHED_PAPER;
+    s->alpha_f = 0.008;
+    s->rho1 = 4.0;
+    s->rho2 = 3.0;
+    s->beta_f = 0.12;
+    s->kappa1 = 0.05;
+    s->kappa2 = 1.0;
+    s->gamma0 = 0.032;
+    s->M = 6;
+    s->hstep = 1.0;
+    s->window = 100;
+    s->n_ambivalent = 0;
+}
+
+void hqa_run_opts_default(hqa_run_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = HQA_PREC_FP32;
+    o->init = HQA_INIT_PAPER;
+}
+
+hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                          const float* val, const float* h, uint32_t flags, hqa_ctx** out)
+{
+    if (!out) return HQA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (N < 1 || N > 65536 || nnz < 0 || !row_ptr || flags != 0) return HQA_ERR_INVALID_ARG;
+    if (nnz > 0 && (!col || !val)) return HQA_ERR_INVALID_ARG;
+    if (row_ptr[0] != 0 || row_ptr[N] != nnz) return HQA_ERR_INVALID_ARG;
+    for (int i = 0; i < N; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return HQA_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (col[k] < 0 || col[k] >= N) return HQA_ERR_INVALID_ARG;
+    if (nnz > 0 && !finite_all(val, (size_t)nnz)) return HQA_ERR_NONFINITE_INPUT;
+    if (h && !finite_all(h, (size_t)N)) return HQA_ERR_NONFINITE_INPUT;
+
+    hqa_ctx* c = new (std::nothrow) hqa_ctx();
+    if (!c) return HQA_ERR_OOM;
+    c->N = N;
+    // sorted rows, diagonal and explicit zeros dropped
+    c->row_ptr.assign(N + 1, 0);
+    std::vector<std::pair<int32_t, float>> rowbuf;
+    for (int i = 0; i < N; ++i) {
+        rowbuf.clear();
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            if (col[k] != i && val[k] != 0.f) rowbuf.emplace_back(col[k], val[k]);
+        std::sort(rowbuf.begin(), rowbuf.end(),
+                  [](const std::pair<int32_t, float>& a, const std::pair<int32_t, float>& b) {
+                      return a.first < b.first;
+                  });
+        for (size_t k = 1; k < rowbuf.size(); ++k)
+            if (rowbuf[k].first == rowbuf[k - 1].first) {
+                delete c;
+                return HQA_ERR_INVALID_ARG;  // duplicate entry
+            }
+        for (auto& e : rowbuf) {
+            c->col.push_back(e.first);
+            c->val.push_back(e.second);
+        }
+        c->row_ptr[i + 1] = (int64_t)c->col.size();
+    }
+    // symmetry: (i, j, v) present iff (j, i, v) present
+    for (int i = 0; i < N; ++i) {
+        for (int64_t k = c->row_ptr[i]; k < c->row_ptr[i + 1]; ++k) {
+            const int j = c->col[k];
+            auto b = c->col.begin() + c->row_ptr[j], e = c->col.begin() + c->row_ptr[j + 1];
+            auto it = std::lower_bound(b, e, i);
+            if (it == e || *it != i || c->val[it - c->col.begin()] != c->val[k]) {
+                delete c;
+                return HQA_ERR_ASYMMETRIC;
+            }
+        }
+    }
+    if (h) c->h.assign(h, h + N);
+    return create_guarded(c, out);
+}
+
+hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t flags,
+                            hqa_ctx** out)
+{
+    if (!out) return HQA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (N < 1 || N > 65536 || !J || flags != 0) return HQA_ERR_INVALID_ARG;
+    const size_t NN = (size_t)N * N;
+    if (!finite_all(J, NN)) return HQA_ERR_NONFINITE_INPUT;
+    if (h && !finite_all(h, (size_t)N)) return HQA_ERR_NONFINITE_INPUT;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j)
+            if (J[(size_t)i * N + j] != J[(size_t)j * N + i]) return HQA_ERR_ASYMMETRIC;
+    hqa_ctx* c = new (std::nothrow) hqa_ctx();
+    if (!c) return HQA_ERR_OOM;
+    c->N = N;
+    c->dense_input = true;
+    c->row_ptr.assign(N + 1, 0);
+    for (int i = 0; i < N; ++i) {
+        for (int j = 0; j < N; ++j) {
+            const float v = J[(size_t)i * N + j];
+            if (j != i && v != 0.f) {
+                c->col.push_back(j);
+                c->val.push_back(v);
+            }
+        }
+        c->row_ptr[i + 1] = (int64_t)c->col.size();
+    }
+    if (h) c->h.assign(h, h + N);
+    return create_guarded(c, out);
+}
+
+hqa_status hqa_ctx_info(const hqa_ctx* ctx, int32_t* N, int64_t* nnz, int32_t* integer_couplings)
+{
+    if (!ctx) return HQA_ERR_INVALID_ARG;
+    if (N) *N = ctx->N;
+    if (nnz) *nnz = ctx->nnz;
+    if (integer_couplings) *integer_couplings = ctx->integer ? 1 : 0;
+    return HQA_OK;
+}
+
+hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+                   int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
+                   const hqa_result* out, void* stream)
+{
+    if (!ctx || !out || replicas < 1) return HQA_ERR_INVALID_ARG;
+    hqa_status s = check_schedule(sched, dt, steps);
+    if (s != HQA_OK) return s;
+    hqa_run_opts o;
+    if (opts) o = *opts;
+    else hqa_run_opts_default(&o);
+    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16) return HQA_ERR_INVALID_ARG;
+    if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_GIVEN) return HQA_ERR_INVALID_ARG;
+    if (o.init == HQA_INIT_GIVEN && (!o.phi0 || !o.p0)) return HQA_ERR_INVALID_ARG;
+    const int rbq = o.replicas_per_block;
+    if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
+        return HQA_ERR_INVALID_ARG;
+    if (misaligned(out->phi, 4) || misaligned(out->p, 4) || misaligned(out->phibar, 4) ||
+        misaligned(out->energy, 8) || misaligned(out->cut, 8) || misaligned(out->tally, 4) ||
+        misaligned(o.phi0, 4) || misaligned(o.p0, 4))
+        return HQA_ERR_INVALID_ARG;
+    const bool want_readout = out->spins || out->frozen || out->tally || out->energy || out->cut;
+    const bool want_energy = out->energy || out->cut;
+    if (want_energy && !ctx->integer) return HQA_ERR_UNSUPPORTED;
+    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    const int RB = rbq ? rbq : hqa_sparse_pick_rb(ctx, replicas, o.precision);
+    if (RB == 0 || hqa_sparse_smem_bytes(ctx, RB, o.precision) > ctx->smem_optin)
+        return HQA_ERR_TOO_LARGE;
+    const SparsePlan* plan = nullptr;
+    s = hqa_sparse_plan(ctx, RB, o.precision, &plan);
+    if (s != HQA_OK) return s;
+    s = upload_schedule(ctx, sched, dt, steps);
+    if (s != HQA_OK) return s;
+
+    // temporaries for outputs the caller skipped but later stages need
+    const size_t RN = (size_t)replicas * ctx->N;
+    size_t need = 0;
+    const bool tmp_phibar = want_readout && !out->phibar;
+    const bool tmp_spins = want_energy && !out->spins;
+    if (tmp_phibar) need += RN * sizeof(float);
+    if (tmp_spins) need += RN;
+    if (need) {
+        s = hqa_reserve(&ctx->d_ws, &ctx->ws_cap, need);
+        if (s != HQA_OK) return s;
+    }
+    char* ws = static_cast<char*>(ctx->d_ws);
+    float* phibar = out->phibar;
+    if (tmp_phibar) {
+        phibar = reinterpret_cast<float*>(ws);
+        ws += RN * sizeof(float);
+    }
+    int8_t* spins = out->spins;
+    if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
+
+    s = hqa_sparse_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
+                             o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
+    if (s != HQA_OK) return s;
+    if (want_readout) {
+        s = hqa_launch_readout(ctx, replicas, phibar, sched->n_ambivalent, spins, out->frozen,
+                               out->tally, st);
+        if (s != HQA_OK) return s;
+    }
+    if (want_energy) {
+        s = hqa_launch_energy(ctx, replicas, spins, out->energy, out->cut, st);
+        if (s != HQA_OK) return s;
+    }
+    return HQA_OK;
+}
+
+hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
+                           int32_t precision, void* stream)
+{
+    if (!ctx || replicas < 1 || !phi || !L || misaligned(phi, 4) || misaligned(L, 4))
+        return HQA_ERR_INVALID_ARG;
+    if (precision != HQA_PREC_FP32 && precision != HQA_PREC_BF16) return HQA_ERR_INVALID_ARG;
+    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
+    const int RB = hqa_sparse_pick_rb(ctx, replicas, precision);
+    if (RB == 0) return HQA_ERR_TOO_LARGE;
+    const SparsePlan* plan = nullptr;
+    hqa_status s = hqa_sparse_plan(ctx, RB, precision, &plan);
+    if (s != HQA_OK) return s;
+    return hqa_sparse_launch_field(ctx, plan, replicas, phi, L, static_cast<cudaStream_t>(stream));
+}
+
+hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
+                       int8_t* spins, uint8_t* frozen, int32_t* tally, void* stream)
+{
+    if (!ctx || replicas < 1 || !phibar || (!spins && !frozen && !tally)) return HQA_ERR_INVALID_ARG;
+    if (misaligned(phibar, 4) || misaligned(tally, 4)) return HQA_ERR_INVALID_ARG;
+    return hqa_launch_readout(ctx, replicas, phibar, n, spins, frozen, tally,
+                              static_cast<cudaStream_t>(stream));
+}
+
+hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
+                      int64_t* cut, void* stream)
+{
+    if (!ctx || replicas < 1 || !spins || (!energy && !cut)) return HQA_ERR_INVALID_ARG;
+    if (misaligned(energy, 8) || misaligned(cut, 8)) return HQA_ERR_INVALID_ARG;
+    return hqa_launch_energy(ctx, replicas, spins, energy, cut, static_cast<cudaStream_t>(stream));
+}
+
+hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                         const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                         int64_t* out_energy, void* stream)
+{
+    if (!ctx || replicas < 1 || !spins || !frozen || !out_spins) return HQA_ERR_INVALID_ARG;
+    if (n < 0 || misaligned(out_energy, 8)) return HQA_ERR_INVALID_ARG;
+    return hqa_launch_subsolve(ctx, replicas, spins, frozen, n, out_spins, out_energy,
+                               static_cast<cudaStream_t>(stream));
+}
+
+hqa_status hqa_sync(hqa_ctx* ctx, void* stream)
+{
+    if (!ctx) return HQA_ERR_INVALID_ARG;
+    HQA_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    uint32_t bits = 0;
+    HQA_CUDA_TRY(cudaMemcpy(&bits, ctx->d_status, sizeof(bits), cudaMemcpyDeviceToHost));
+    if (bits) HQA_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
+    if (bits & HQA_DEV_NONFINITE) return HQA_ERR_NONFINITE;
+    if (bits & HQA_DEV_TIMEOUT) return HQA_ERR_TIMEOUT;
+    if (bits & HQA_DEV_BAD_SUBPROBLEM) return HQA_ERR_INVALID_ARG;
+    return HQA_OK;
+}
+
+const char* hqa_status_string(hqa_status s)
+{
+    switch (s) {
+    case HQA_OK: return "ok";
+    case HQA_ERR_INVALID_ARG: return "invalid argument";
+    case HQA_ERR_ASYMMETRIC: return "coupling matrix is not symmetric";
+    case HQA_ERR_NONFINITE_INPUT: return "non-finite coupling or field";
+    case HQA_ERR_OOM: return "device out of memory";
+    case HQA_ERR_CUDA: return "CUDA runtime error";
+    case HQA_ERR_UNSUPPORTED: return "unsupported by this build";
+    case HQA_ERR_NONFINITE: return "trajectory became non-finite";
+    case HQA_ERR_TIMEOUT: return "device-side wait timed out";
+    case HQA_ERR_TOO_LARGE: return "size beyond a documented limit";
+    }
+    return "unknown status";
+}
+
+void hqa_destroy(hqa_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_ctx_device(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

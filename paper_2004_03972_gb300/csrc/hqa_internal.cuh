@@ -1,0 +1,121 @@
+// hqa_internal.cuh -- context layout, status bits and launch helpers shared by
+// the library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "../../include/hqa.h"
+
+// Device-side status bits, OR-ed into ctx->d_status by kernels.
+enum : uint32_t {
+    HQA_DEV_NONFINITE = 1u << 0,
+    HQA_DEV_BAD_SUBPROBLEM = 1u << 1,
+    HQA_DEV_TIMEOUT = 1u << 2,
+};
+
+#define HQA_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            (void)cudaGetLastError();                        \
+            return _e == cudaErrorMemoryAllocation ? HQA_ERR_OOM : HQA_ERR_CUDA; \
+        }                                                    \
+    } while (0)
+
+// One step of the kick/drift coefficient table (see hqa_run).
+struct StepCoef {
+    float kA;  // c_j h alpha(j dt) M       multiplies phi^(M-1)
+    float kB;  // c_j h beta(j dt)          multiplies the local field
+    float dA;  // h alpha((j + 1/2) dt)     multiplies p in the drift
+    float pad;
+};
+
+// Resident sparse plan for one (replicas-per-block, operand precision).
+// Rows are grouped into "tuples" of G = 32 / RB rows; one warp evaluates a
+// tuple with lane = (row slot g, replica r).  Each tuple's neighbour lists
+// are padded to a common length, split into an all-positive and an
+// all-negative section, and packed as chunks of 4 byte offsets per lane.
+struct SparsePlan {
+    int RB = 0, G = 0, T = 0, Npad = 0, prec = 0;
+    int64_t chunks = 0;
+    uint4* d_entries = nullptr;   // [chunk][G] uint4: byte offsets of phi rows in one buffer
+    int4* d_tuples = nullptr;     // [T] {first chunk, positive chunks, negative chunks, 0}
+    int* d_tuple_rows = nullptr;  // [T][G] row index or -1
+    double pad_ratio = 0.0;       // stored positions / nnz
+    double conflict_ratio = 0.0;  // bank wavefronts / conflict-free wavefronts (host model)
+};
+
+struct hqa_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    int32_t N = 0;
+    int64_t nnz = 0;            // stored off-diagonal entries (both triangles)
+    bool dense_input = false;
+    bool integer = false;       // all J and h integral with |J| <= 127, |h| <= 2^20
+    bool unit = false;          // all J in {-1, 0, +1}
+    bool has_h = false;
+
+    // host copies of the symmetric CSR (diagonal dropped), used to build plans
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    std::vector<float> val;
+    std::vector<float> h;
+
+    // device copies
+    int32_t* d_row_ptr = nullptr;  // N+1 (int32: nnz < 2^31 enforced)
+    int32_t* d_col = nullptr;
+    float* d_val = nullptr;
+    int8_t* d_val_i8 = nullptr;    // integer path
+    float* d_h = nullptr;          // N or null
+    int32_t* d_h_i32 = nullptr;    // integer path
+    int64_t sum_J_all = 0;         // sum of all stored entries (integer path)
+
+    std::map<int, SparsePlan> plans;   // key = RB * 16 + prec
+
+    // schedule table cache
+    std::vector<StepCoef> sched_host;
+    StepCoef* d_sched = nullptr;
+    size_t sched_cap = 0;
+
+    // grow-only workspaces: run temporaries, MD state spilled from shared
+    // memory, sub-solve scratch
+    void* d_ws = nullptr;
+    size_t ws_cap = 0;
+    void* d_state = nullptr;
+    size_t state_cap = 0;
+    void* d_sub = nullptr;
+    size_t sub_cap = 0;
+    uint32_t* d_status = nullptr;
+};
+
+// Ensures *p holds at least `bytes` device bytes (frees and reallocates;
+// cudaFree synchronises the device, so in-flight users are finished).
+hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes);
+
+// sparse_md.cu
+hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out);
+int hqa_sparse_pick_rb(const hqa_ctx* ctx, int32_t R, int prec);
+size_t hqa_sparse_smem_bytes(const hqa_ctx* ctx, int RB, int prec);
+hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const StepCoef* d_sched,
+                                int64_t S, int32_t W, int32_t R, uint64_t seed, int init,
+                                const float* phi0, const float* p0, int M, float* phi_out,
+                                float* p_out, float* phibar_out, cudaStream_t st);
+hqa_status hqa_sparse_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t R,
+                                   const float* phi, float* L, cudaStream_t st);
+
+// readout.cu
+hqa_status hqa_launch_readout(hqa_ctx* ctx, int32_t R, const float* phibar, int32_t n,
+                              int8_t* spins, uint8_t* frozen, int32_t* tally, cudaStream_t st);
+hqa_status hqa_launch_energy(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,
+                             int64_t* cut, cudaStream_t st);
+
+// subsolve.cu
+hqa_status hqa_launch_subsolve(hqa_ctx* ctx, int32_t R, const int8_t* spins,
+                               const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                               int64_t* out_energy, cudaStream_t st);

@@ -1,0 +1,261 @@
+"""ctypes binding of libhqa.so (include/hqa.h).
+
+Argument marshalling only: every step of HQA-MD runs in the CUDA library.
+PyTorch supplies device memory and the current CUDA stream.  If the library
+has not been built, ``lib()`` raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhqa.so")
+
+HQA_OK = 0
+STATUS_NAMES = {
+    0: "HQA_OK", 1: "HQA_ERR_INVALID_ARG", 2: "HQA_ERR_ASYMMETRIC", 3: "HQA_ERR_NONFINITE_INPUT",
+    4: "HQA_ERR_OOM", 5: "HQA_ERR_CUDA", 6: "HQA_ERR_UNSUPPORTED", 7: "HQA_ERR_NONFINITE",
+    8: "HQA_ERR_TIMEOUT", 9: "HQA_ERR_TOO_LARGE",
+}
+SCHED_PAPER, SCHED_LINEAR_GAMMA, SCHED_TABLE = 0, 1, 2
+INIT_PAPER, INIT_RANDOM_FLUX, INIT_GIVEN = 0, 1, 2
+PREC_FP32, PREC_BF16 = 0, 1
+
+# every symbol include/hqa.h declares
+EXPORTS = (
+    "hqa_schedule_default", "hqa_run_opts_default", "hqa_create_dense", "hqa_create_csr",
+    "hqa_ctx_info", "hqa_run", "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
+    "hqa_sync", "hqa_status_string", "hqa_destroy",
+)
+
+
+class HQAError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+
+
+class Schedule(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32),
+        ("alpha_f", C.c_double), ("rho1", C.c_double), ("rho2", C.c_double),
+        ("beta_f", C.c_double), ("kappa1", C.c_double), ("kappa2", C.c_double),
+        ("gamma0", C.c_double),
+        ("M", C.c_int32),
+        ("hstep", C.c_double),
+        ("window", C.c_int32),
+        ("n_ambivalent", C.c_int32),
+        ("table_alpha", C.c_void_p),
+        ("table_beta", C.c_void_p),
+    ]
+
+
+class RunOpts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32),
+        ("init", C.c_int32),
+        ("phi0", C.c_void_p),
+        ("p0", C.c_void_p),
+        ("replicas_per_block", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in
+                ("phi", "p", "phibar", "spins", "frozen", "energy", "cut", "tally")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libhqa.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, u64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_uint32
+            L.hqa_schedule_default.argtypes = [C.POINTER(Schedule)]
+            L.hqa_run_opts_default.argtypes = [C.POINTER(RunOpts)]
+            L.hqa_create_dense.argtypes = [i32, vp, vp, u32, C.POINTER(vp)]
+            L.hqa_create_csr.argtypes = [i32, i64, vp, vp, vp, vp, u32, C.POINTER(vp)]
+            L.hqa_ctx_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            L.hqa_run.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i32, u64,
+                                  C.POINTER(RunOpts), C.POINTER(Result), vp]
+            L.hqa_local_field.argtypes = [vp, i32, vp, vp, i32, vp]
+            L.hqa_readout.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
+            L.hqa_energy.argtypes = [vp, i32, vp, vp, vp, vp]
+            L.hqa_solve_sub.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
+            L.hqa_sync.argtypes = [vp, vp]
+            L.hqa_status_string.argtypes = [C.c_int]
+            L.hqa_status_string.restype = C.c_char_p
+            L.hqa_destroy.argtypes = [vp]
+            L.hqa_destroy.restype = None
+            for name in ("hqa_create_dense", "hqa_create_csr", "hqa_ctx_info", "hqa_run",
+                         "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
+                         "hqa_sync"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != HQA_OK:
+        raise HQAError(st, what)
+
+
+def schedule(**kw) -> Schedule:
+    """The paper's schedule (hqa_schedule_default) with keyword overrides."""
+    s = Schedule()
+    lib().hqa_schedule_default(C.byref(s))
+    for k, v in kw.items():
+        if k in ("table_alpha", "table_beta"):
+            raise ValueError("use table=(alpha, beta) for HQA_SCHED_TABLE")
+        setattr(s, k, v)
+    return s
+
+
+def _stream_ptr(stream=None):
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(st.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns an hqa_ctx (device copies of the couplings)."""
+
+    def __init__(self, handle: C.c_void_p, N: int):
+        self._h = handle
+        self.N = N
+
+    @classmethod
+    def from_dense(cls, J, h=None):
+        J = np.ascontiguousarray(J, dtype=np.float32)
+        N = J.shape[0]
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
+        out = C.c_void_p()
+        _check(lib().hqa_create_dense(N, J.ctypes.data, None if hh is None else hh.ctypes.data,
+                                      0, C.byref(out)), "hqa_create_dense")
+        return cls(out, N)
+
+    @classmethod
+    def from_csr(cls, N, row_ptr, col, val, h=None):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cc = np.ascontiguousarray(col, dtype=np.int32)
+        vv = np.ascontiguousarray(val, dtype=np.float32)
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
+        out = C.c_void_p()
+        _check(lib().hqa_create_csr(int(N), int(rp[-1]), rp.ctypes.data, cc.ctypes.data,
+                                    vv.ctypes.data, None if hh is None else hh.ctypes.data, 0,
+                                    C.byref(out)), "hqa_create_csr")
+        return cls(out, int(N))
+
+    @classmethod
+    def from_instance(cls, inst):
+        if inst.dense is not None:
+            return cls.from_dense(inst.dense, inst.h)
+        return cls.from_csr(inst.N, inst.row_ptr, inst.col, inst.val, inst.h)
+
+    def info(self):
+        N, nnz, integ = C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib().hqa_ctx_info(self._h, C.byref(N), C.byref(nnz), C.byref(integ)), "hqa_ctx_info")
+        return {"N": N.value, "nnz": nnz.value, "integer": bool(integ.value)}
+
+    def run(self, steps, replicas, seed=0, sched=None, dt=None, precision=PREC_FP32,
+            init=INIT_PAPER, phi0=None, p0=None, replicas_per_block=0, outputs=None,
+            out=None, stream=None, table=None):
+        """hqa_run. Returns a dict of device tensors (phi, p, phibar, spins, frozen, energy,
+        cut, tally) -- those named in ``outputs`` (default: all), or the caller's ``out``."""
+        import torch
+        R, N = int(replicas), self.N
+        sched = sched if sched is not None else schedule()
+        keep = []
+        if table is not None:
+            ta = np.ascontiguousarray(table[0], dtype=np.float64)
+            tb = np.ascontiguousarray(table[1], dtype=np.float64)
+            keep += [ta, tb]
+            sched.kind = SCHED_TABLE
+            sched.table_alpha = ta.ctypes.data
+            sched.table_beta = tb.ctypes.data
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        opts.init = init
+        opts.phi0 = None if phi0 is None else phi0.data_ptr()
+        opts.p0 = None if p0 is None else p0.data_ptr()
+        opts.replicas_per_block = replicas_per_block
+        if out is None:
+            dev = torch.device("cuda")
+            names = outputs or ("phi", "p", "phibar", "spins", "frozen", "energy", "cut", "tally")
+            shapes = {"phi": ((R, N), torch.float32), "p": ((R, N), torch.float32),
+                      "phibar": ((R, N), torch.float32), "spins": ((R, N), torch.int8),
+                      "frozen": ((R, N), torch.uint8), "energy": ((R,), torch.int64),
+                      "cut": ((R,), torch.int64), "tally": ((R, 2), torch.int32)}
+            out = {k: torch.empty(*shapes[k][:1], dtype=shapes[k][1], device=dev) for k in names}
+        res = Result(**{k: (v.data_ptr() if v is not None else None) for k, v in out.items()})
+        dt = (1.0 / steps if steps > 0 else 1.0) if dt is None else dt
+        _check(lib().hqa_run(self._h, C.byref(sched), float(dt), int(steps), R, int(seed),
+                             C.byref(opts), C.byref(res), _stream_ptr(stream)), "hqa_run")
+        del keep
+        return out
+
+    def local_field(self, phi, precision=PREC_FP32, stream=None):
+        import torch
+        R = phi.shape[0]
+        L = torch.empty_like(phi)
+        _check(lib().hqa_local_field(self._h, R, _ptr(phi), _ptr(L), precision,
+                                     _stream_ptr(stream)), "hqa_local_field")
+        return L
+
+    def readout(self, phibar, n, stream=None):
+        import torch
+        R, N = phibar.shape
+        spins = torch.empty((R, N), dtype=torch.int8, device=phibar.device)
+        frozen = torch.empty((R, N), dtype=torch.uint8, device=phibar.device)
+        tally = torch.empty((R, 2), dtype=torch.int32, device=phibar.device)
+        _check(lib().hqa_readout(self._h, R, _ptr(phibar), int(n), _ptr(spins), _ptr(frozen),
+                                 _ptr(tally), _stream_ptr(stream)), "hqa_readout")
+        return spins, frozen, tally
+
+    def energy(self, spins, stream=None):
+        import torch
+        R = spins.shape[0]
+        e = torch.empty(R, dtype=torch.int64, device=spins.device)
+        c = torch.empty(R, dtype=torch.int64, device=spins.device)
+        _check(lib().hqa_energy(self._h, R, _ptr(spins), _ptr(e), _ptr(c), _stream_ptr(stream)),
+               "hqa_energy")
+        return e, c
+
+    def solve_sub(self, spins, frozen, n, stream=None):
+        import torch
+        R = spins.shape[0]
+        out = torch.empty_like(spins)
+        e = torch.empty(R, dtype=torch.int64, device=spins.device)
+        _check(lib().hqa_solve_sub(self._h, R, _ptr(spins), _ptr(frozen), int(n), _ptr(out),
+                                   _ptr(e), _stream_ptr(stream)), "hqa_solve_sub")
+        return out, e
+
+    def sync(self, stream=None):
+        _check(lib().hqa_sync(self._h, _stream_ptr(stream)), "hqa_sync (latched device status)")
+
+    def close(self):
+        if self._h:
+            lib().hqa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,86 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a GPU,
+exports every function include/hqa.h declares, and the ctypes structures have
+the C layout (checked against a host program compiled from the header)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hqa.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2004_03972_gb300 import build, hqa
+    build.build()
+    return hqa.lib()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(?:hqa_status|void|const char\s*\*)\s+(hqa_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2004_03972_gb300 import hqa
+    assert sorted(hqa.EXPORTS) == names
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2004_03972_gb300 import hqa
+    for code in range(10):
+        assert lib.hqa_status_string(code)
+    s = hqa.schedule()
+    assert (s.kind, s.alpha_f, s.rho1, s.rho2) == (0, 0.008, 4.0, 3.0)
+    assert (s.beta_f, s.kappa1, s.kappa2, s.M, s.hstep, s.window) == (0.12, 0.05, 1.0, 6, 1.0, 100)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    import ctypes as C
+    from paper_2004_03972_gb300 import hqa
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "hqa.h"\n'
+        "#define P(T, f) printf(#T \" \" #f \" %zu\\n\", offsetof(T, f));\n"
+        "int main(void) {\n"
+        " printf(\"hqa_schedule size %zu\\n\", sizeof(hqa_schedule));\n"
+        " printf(\"hqa_run_opts size %zu\\n\", sizeof(hqa_run_opts));\n"
+        " printf(\"hqa_result size %zu\\n\", sizeof(hqa_result));\n"
+        + "".join(f" P(hqa_schedule, {f})\n" for f, _ in hqa.Schedule._fields_)
+        + "".join(f" P(hqa_run_opts, {f})\n" for f, _ in hqa.RunOpts._fields_)
+        + "".join(f" P(hqa_result, {f})\n" for f, _ in hqa.Result._fields_)
+        + " return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    table = {"hqa_schedule": hqa.Schedule, "hqa_run_opts": hqa.RunOpts, "hqa_result": hqa.Result}
+    for line in got:
+        if not line:
+            continue
+        t, f, v = line.split()
+        if f == "size":
+            assert C.sizeof(table[t]) == int(v), t
+        else:
+            assert getattr(table[t], f).offset == int(v), (t, f)
+
+
+def test_library_has_no_cuda_runtime_dependency(lib):
+    from paper_2004_03972_gb300 import hqa
+    out = subprocess.run(["ldd", hqa.LIB_PATH], capture_output=True, text=True).stdout
+    assert "libcudart" not in out   # static runtime: loads on hosts without the toolkit
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2004_03972_gb300 import hqa
+    monkeypatch.setattr(hqa, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(hqa, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        hqa.lib()
