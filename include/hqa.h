@@ -217,6 +217,27 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
                          const uint8_t* frozen, int32_t n, int8_t* out_spins,
                          int64_t* out_energy, void* stream);
 
+/* hqa_solve_sub without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot let the library call
+ * cudaMalloc -- a process whose device memory is already reserved by
+ * another allocator or arena, or a latency-sensitive caller that cannot
+ * accept cudaMalloc's implicit device-wide synchronisation.  Same arguments,
+ * results and errors as hqa_solve_sub; the caller still provides every
+ * input and output buffer.
+ * Scratch: a fixed array compiled into the library (about 1.1 MB, enough for
+ * 2048 replicas), present on every GPU that loads the library until the
+ * process exits.  replicas > 2048 returns HQA_ERR_TOO_LARGE.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the context's device current); make that first call before
+ * any stream capture.  The current device must be the context's device
+ * (HQA_ERR_INVALID_ARG otherwise).
+ * Every call shares the one array and leaves its contents behind; each call
+ * rewrites what it reads before reading it.  Calls whose work overlaps on
+ * the GPU (for example on two streams) race: serialise them. */
+hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                                 const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                                 int64_t* out_energy, void* stream);
+
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream);

@@ -12,6 +12,9 @@
 // order (step t flips bit ctz(t)); the best (H', x) pair, ties to the
 // smallest x, is reduced by warp shuffles and one 64-bit atomicMin per CTA
 // on the key ((H' + 2^31) << 32 | x).
+#include <atomic>
+#include <mutex>
+
 #include "hqa_internal.cuh"
 
 namespace {
@@ -255,6 +258,95 @@ hqa_status hqa_launch_subsolve(hqa_ctx* ctx, int32_t R, const int8_t* spins,
     const int LB = pick_lb(R, n, ctx->sm_count);
     const int HB = n - LB;
     const uint32_t per = 1u << HB;
+    const dim3 grid((per + kEnumThreads - 1) / kEnumThreads, R);
+    k_sub_enum<<<grid, kEnumThreads, 0, st>>>(prep, LB, keys);
+    k_sub_assemble<<<R, 256, 0, st>>>(prep, keys, ctx->N, spins, out_spins);
+    if (cudaGetLastError() != cudaSuccess) return HQA_ERR_CUDA;
+    if (out_energy) return hqa_launch_energy(ctx, R, out_spins, out_energy, nullptr, st);
+    return HQA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the sub-solve.
+//
+// Some callers cannot let the library call cudaMalloc: processes whose device
+// memory is reserved up front by another allocator or arena (nothing is left
+// to hand out), and latency-sensitive callers for whom cudaMalloc's implicit
+// device-wide synchronisation is not acceptable.  This entry point runs the
+// same three kernels as hqa_solve_sub, but its scratch (the per-replica
+// reduced-problem records and the 64-bit argmin keys) lives in the
+// file-scope array below, which every GPU that loads the library holds until
+// the process exits.  The records and keys of each replica are rewritten by
+// k_sub_prep before they are read, so stale contents from the previous call
+// are never used.  All calls share the one array: calls whose kernels
+// overlap on the GPU (e.g. on two streams) race and must be serialised by
+// the caller.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocMaxReplicas = 2048;
+constexpr size_t kNoAllocKeysOff =
+    ((size_t)kNoAllocMaxReplicas * sizeof(SubPrep) + 255) & ~(size_t)255;
+constexpr size_t kNoAllocBytes = kNoAllocKeysOff + (size_t)kNoAllocMaxReplicas * 8;
+constexpr int kMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_sub_scratch[kNoAllocBytes];
+
+// Device address of g_sub_scratch per device ordinal.  In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress once per device (with that device current).
+static std::atomic<unsigned char*> g_sub_scratch_dev[kMaxDevices];
+static std::mutex g_sub_scratch_mu;
+
+static hqa_status sub_scratch_address(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return HQA_ERR_UNSUPPORTED;
+    unsigned char* p = g_sub_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lk(g_sub_scratch_mu);
+        p = g_sub_scratch_dev[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            void* a = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&a, g_sub_scratch);
+            if (e != cudaSuccess || !a) {
+                (void)cudaGetLastError();
+                return HQA_ERR_CUDA;
+            }
+            p = static_cast<unsigned char*>(a);
+            g_sub_scratch_dev[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return HQA_OK;
+}
+
+extern "C" hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                                            const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                                            int64_t* out_energy, void* stream)
+{
+    if (!ctx || replicas < 1 || !spins || !frozen || !out_spins || n < 0) return HQA_ERR_INVALID_ARG;
+    if (out_energy && ((uintptr_t)out_energy % 8) != 0) return HQA_ERR_INVALID_ARG;
+    if (replicas > kNoAllocMaxReplicas) return HQA_ERR_TOO_LARGE;  // scratch holds 2048 replicas
+    if (!ctx->integer || !ctx->unit) return HQA_ERR_UNSUPPORTED;
+    if (n > kMaxN) return HQA_ERR_TOO_LARGE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HQA_ERR_CUDA;
+    }
+    if (dev != ctx->device) return HQA_ERR_INVALID_ARG;  // the scratch address is per device
+    unsigned char* base = nullptr;
+    hqa_status s = sub_scratch_address(dev, &base);
+    if (s != HQA_OK) return s;
+    SubPrep* prep = reinterpret_cast<SubPrep*>(base);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + kNoAllocKeysOff);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int32_t R = replicas;
+    k_sub_prep<<<R, kPrepThreads, 0, st>>>(ctx->d_row_ptr, ctx->d_col, ctx->d_val_i8,
+                                           ctx->has_h ? ctx->d_h_i32 : nullptr, ctx->N, n, spins,
+                                           frozen, prep, keys, ctx->d_status);
+    const int LB = pick_lb(R, n, ctx->sm_count);
+    const uint32_t per = 1u << (n - LB);
     const dim3 grid((per + kEnumThreads - 1) / kEnumThreads, R);
     k_sub_enum<<<grid, kEnumThreads, 0, st>>>(prep, LB, keys);
     k_sub_assemble<<<R, 256, 0, st>>>(prep, keys, ctx->N, spins, out_spins);

@@ -29,7 +29,7 @@ PREC_FP32, PREC_BF16 = 0, 1
 EXPORTS = (
     "hqa_schedule_default", "hqa_run_opts_default", "hqa_create_dense", "hqa_create_csr",
     "hqa_ctx_info", "hqa_run", "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
-    "hqa_sync", "hqa_status_string", "hqa_destroy",
+    "hqa_solve_sub_noalloc", "hqa_sync", "hqa_status_string", "hqa_destroy",
 )
 
 
@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
             L.hqa_readout.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
             L.hqa_energy.argtypes = [vp, i32, vp, vp, vp, vp]
             L.hqa_solve_sub.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
+            L.hqa_solve_sub_noalloc.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
             L.hqa_sync.argtypes = [vp, vp]
             L.hqa_status_string.argtypes = [C.c_int]
             L.hqa_status_string.restype = C.c_char_p
@@ -100,7 +101,7 @@ def lib() -> C.CDLL:
             L.hqa_destroy.restype = None
             for name in ("hqa_create_dense", "hqa_create_csr", "hqa_ctx_info", "hqa_run",
                          "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
-                         "hqa_sync"):
+                         "hqa_solve_sub_noalloc", "hqa_sync"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -245,6 +246,15 @@ class Context:
         _check(lib().hqa_solve_sub(self._h, R, _ptr(spins), _ptr(frozen), int(n), _ptr(out),
                                    _ptr(e), _stream_ptr(stream)), "hqa_solve_sub")
         return out, e
+
+    def solve_sub_noalloc(self, spins, frozen, n, out_spins, out_energy=None, stream=None):
+        """hqa_solve_sub_noalloc: the sub-solve with the library's fixed scratch array,
+        for callers that cannot let the library allocate device memory.  The caller
+        passes the output buffers; nothing is allocated here or in the library."""
+        _check(lib().hqa_solve_sub_noalloc(self._h, spins.shape[0], _ptr(spins), _ptr(frozen),
+                                           int(n), _ptr(out_spins), _ptr(out_energy),
+                                           _stream_ptr(stream)), "hqa_solve_sub_noalloc")
+        return out_spins, out_energy
 
     def sync(self, stream=None):
         _check(lib().hqa_sync(self._h, _stream_ptr(stream)), "hqa_sync (latched device status)")
