@@ -280,8 +280,11 @@ def run_ours(args):
     achieved = bytes_per_launch / t_md / 1e9
     mhz = clk.get("sm_max_mhz") or 2070.0
     peak_smem = sm_count * 128 * mhz * 1e6 / 1e9    # GB/s: 128 B/clk/SM shared-memory bandwidth
-    rb = 8
-    traffic = ncu_traffic(f"k_sparse_md<{rb},{'true' if head == 'bf16' else 'false'}>@{args.config}")
+    plan = ctx.plan(R, precision=variants[head]["prec"])
+    rb = plan["replicas_per_block"]
+    kname = ("k_sparse_md_vec" if plan["kernel"] == hqa.KERNEL_VECTOR else "k_sparse_md") + \
+        f"<{rb},{'true' if head == 'bf16' else 'false'}>"
+    traffic = ncu_traffic(f"{kname}@{args.config}")
 
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
     line = {
@@ -304,7 +307,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak_smem, "unit": "GB/s",
                      "frac": achieved / peak_smem, "traffic": traffic,
-                     "kernel": f"k_sparse_md<{rb},{'true' if head == 'bf16' else 'false'}>",
+                     "kernel": kname, "plan": plan,
                      "peak_source": "derived: SMs x 128 B/clk x max SM clock (shared-memory bandwidth)"},
         "clocks": clk,
     }

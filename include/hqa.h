@@ -89,12 +89,21 @@ enum {
     HQA_PREC_BF16 = 1  /* phi operand rounded to BF16, FP32 accumulate; phi, p stay FP32 */
 };
 
+/* Sparse kernel variants (both compute the same sums, in different orders). */
+enum {
+    HQA_KERNEL_AUTO = 0,   /* vectorised when the blocking allows, else scalar */
+    HQA_KERNEL_SCALAR = 1, /* one replica per lane, neighbour lists streamed from L1/L2 */
+    HQA_KERNEL_VECTOR = 2  /* 16-byte gathers per lane, lists in shared memory; needs
+                              replicas_per_block >= 4 (FP32) or >= 8 (BF16) */
+};
+
 typedef struct {
     int32_t precision;          /* HQA_PREC_*; default FP32 */
     int32_t init;               /* HQA_INIT_*; default PAPER */
     const float* phi0;          /* device [R][N]; HQA_INIT_GIVEN only */
     const float* p0;            /* device [R][N]; HQA_INIT_GIVEN only */
     int32_t replicas_per_block; /* 0 = chosen by the library; else 1,2,4,8,16,32 */
+    int32_t kernel;             /* HQA_KERNEL_*; default AUTO */
 } hqa_run_opts;
 
 /* Caller-owned device outputs of hqa_run ([R][N] unless noted).  Any
@@ -178,9 +187,10 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
 /* Local field of the paper's kick (Methods, "Leapfrog algorithm"):
  *   L_i = sum_{j != i} J_ij phi_j + 2 h_i |phi_i|
  * for R replicas.  phi, L: device [R][N] float.  The sum is evaluated by
- * the same device code as hqa_run's field, in the given precision. */
+ * the same device code hqa_run would use with the same `opts` (precision,
+ * replicas_per_block, kernel; NULL = defaults; init fields are ignored). */
 hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
-                           int32_t precision, void* stream);
+                           const hqa_run_opts* opts, void* stream);
 
 /* Readout (Results, "Sorting frozen and ambivalent variables"; HQA
  * section): s_i = sgn(phibar_i), sgn(0) = +1; spins ordered by
@@ -237,6 +247,25 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
 hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
                                  const uint8_t* frozen, int32_t n, int8_t* out_spins,
                                  int64_t* out_energy, void* stream);
+
+/* Launch plan hqa_run / hqa_local_field would use for `replicas` replicas
+ * with `opts` (NULL = defaults); builds and caches it if needed.  The
+ * modelled figures describe the neighbour-list layout: stored positions per
+ * coupling entry (padding), shared-memory wavefronts per conflict-free
+ * wavefront (bank conflicts), and mean/max warp load (balance). */
+typedef struct {
+    int32_t kernel;              /* HQA_KERNEL_SCALAR or HQA_KERNEL_VECTOR */
+    int32_t replicas_per_block;
+    int32_t blocks;              /* CTAs per launch */
+    int32_t threads;             /* threads per CTA */
+    int64_t smem_bytes;          /* dynamic shared memory per CTA */
+    double pad_ratio;
+    double conflict_ratio;
+    double balance;
+} hqa_plan_info;
+
+hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* opts,
+                          hqa_plan_info* out);
 
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */

@@ -35,6 +35,9 @@ void free_ctx_device(hqa_ctx* c)
         cudaFree(kv.second.d_entries);
         cudaFree(kv.second.d_tuples);
         cudaFree(kv.second.d_tuple_rows);
+        if (kv.second.d_warp_off) cudaFree(kv.second.d_warp_off);
+        if (kv.second.d_slot_of_row) cudaFree(kv.second.d_slot_of_row);
+        if (kv.second.d_tuple_list) cudaFree(kv.second.d_tuple_list);
     }
     c->plans.clear();
     void* ptrs[] = {c->d_row_ptr, c->d_col,  c->d_val, c->d_val_i8, c->d_h,     c->d_h_i32,
@@ -190,6 +193,42 @@ hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t
     return HQA_OK;
 }
 
+hqa_status check_opts(const hqa_run_opts& o)
+{
+    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16) return HQA_ERR_INVALID_ARG;
+    const int rbq = o.replicas_per_block;
+    if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
+        return HQA_ERR_INVALID_ARG;
+    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_VECTOR) return HQA_ERR_INVALID_ARG;
+    return HQA_OK;
+}
+
+// Replica blocking and kernel variant: the vectorised kernel when the
+// blocking allows it and its shared-memory image fits, else the scalar one.
+hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& o, const SparsePlan** plan)
+{
+    int RB = o.replicas_per_block;
+    if (RB == 0) {
+        RB = hqa_sparse_pick_rb(ctx, R, o.precision);
+        // the vectorised kernel needs a full 16-byte vector of replicas per lane
+        const int V = o.precision == HQA_PREC_BF16 ? 8 : 4;
+        if (o.kernel != HQA_KERNEL_SCALAR && RB < V && RB > 0 && R >= V) RB = V;
+    }
+    if (RB == 0) return HQA_ERR_TOO_LARGE;
+    if (o.kernel != HQA_KERNEL_SCALAR && hqa_vec_supported(ctx, RB, o.precision)) {
+        const SparsePlan* vp = nullptr;
+        hqa_status s = hqa_vec_plan(ctx, RB, o.precision, &vp);
+        if (s != HQA_OK) return s;
+        if (hqa_vec_smem_bytes(ctx, RB, o.precision, vp->ent_bytes) <= ctx->smem_optin) {
+            *plan = vp;
+            return HQA_OK;
+        }
+    }
+    if (o.kernel == HQA_KERNEL_VECTOR) return HQA_ERR_UNSUPPORTED;
+    if (hqa_sparse_smem_bytes(ctx, RB, o.precision) > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
+    return hqa_sparse_plan(ctx, RB, o.precision, plan);
+}
+
 }  // namespace
 
 extern "C" {
@@ -326,12 +365,10 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     hqa_run_opts o;
     if (opts) o = *opts;
     else hqa_run_opts_default(&o);
-    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16) return HQA_ERR_INVALID_ARG;
+    s = check_opts(o);
+    if (s != HQA_OK) return s;
     if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_GIVEN) return HQA_ERR_INVALID_ARG;
     if (o.init == HQA_INIT_GIVEN && (!o.phi0 || !o.p0)) return HQA_ERR_INVALID_ARG;
-    const int rbq = o.replicas_per_block;
-    if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
-        return HQA_ERR_INVALID_ARG;
     if (misaligned(out->phi, 4) || misaligned(out->p, 4) || misaligned(out->phibar, 4) ||
         misaligned(out->energy, 8) || misaligned(out->cut, 8) || misaligned(out->tally, 4) ||
         misaligned(o.phi0, 4) || misaligned(o.p0, 4))
@@ -342,11 +379,8 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    const int RB = rbq ? rbq : hqa_sparse_pick_rb(ctx, replicas, o.precision);
-    if (RB == 0 || hqa_sparse_smem_bytes(ctx, RB, o.precision) > ctx->smem_optin)
-        return HQA_ERR_TOO_LARGE;
     const SparsePlan* plan = nullptr;
-    s = hqa_sparse_plan(ctx, RB, o.precision, &plan);
+    s = choose_plan(ctx, replicas, o, &plan);
     if (s != HQA_OK) return s;
     s = upload_schedule(ctx, sched, dt, steps);
     if (s != HQA_OK) return s;
@@ -371,8 +405,12 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     int8_t* spins = out->spins;
     if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
 
-    s = hqa_sparse_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
-                             o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
+    if (plan->vec)
+        s = hqa_vec_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
+                              o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
+    else
+        s = hqa_sparse_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed,
+                                 o.init, o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
     if (s != HQA_OK) return s;
     if (want_readout) {
         s = hqa_launch_readout(ctx, replicas, phibar, sched->n_ambivalent, spins, out->frozen,
@@ -387,18 +425,22 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
 }
 
 hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
-                           int32_t precision, void* stream)
+                           const hqa_run_opts* opts, void* stream)
 {
     if (!ctx || replicas < 1 || !phi || !L || misaligned(phi, 4) || misaligned(L, 4))
         return HQA_ERR_INVALID_ARG;
-    if (precision != HQA_PREC_FP32 && precision != HQA_PREC_BF16) return HQA_ERR_INVALID_ARG;
-    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
-    const int RB = hqa_sparse_pick_rb(ctx, replicas, precision);
-    if (RB == 0) return HQA_ERR_TOO_LARGE;
-    const SparsePlan* plan = nullptr;
-    hqa_status s = hqa_sparse_plan(ctx, RB, precision, &plan);
+    hqa_run_opts o;
+    if (opts) o = *opts;
+    else hqa_run_opts_default(&o);
+    hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    return hqa_sparse_launch_field(ctx, plan, replicas, phi, L, static_cast<cudaStream_t>(stream));
+    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
+    const SparsePlan* plan = nullptr;
+    s = choose_plan(ctx, replicas, o, &plan);
+    if (s != HQA_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plan->vec) return hqa_vec_launch_field(ctx, plan, replicas, phi, L, st);
+    return hqa_sparse_launch_field(ctx, plan, replicas, phi, L, st);
 }
 
 hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
@@ -426,6 +468,35 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
     if (n < 0 || misaligned(out_energy, 8)) return HQA_ERR_INVALID_ARG;
     return hqa_launch_subsolve(ctx, replicas, spins, frozen, n, out_spins, out_energy,
                                static_cast<cudaStream_t>(stream));
+}
+
+hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* opts,
+                          hqa_plan_info* out)
+{
+    if (!ctx || replicas < 1 || !out) return HQA_ERR_INVALID_ARG;
+    hqa_run_opts o;
+    if (opts) o = *opts;
+    else hqa_run_opts_default(&o);
+    hqa_status s = check_opts(o);
+    if (s != HQA_OK) return s;
+    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
+    const SparsePlan* plan = nullptr;
+    s = choose_plan(ctx, replicas, o, &plan);
+    if (s != HQA_OK) return s;
+    out->kernel = plan->vec ? HQA_KERNEL_VECTOR : HQA_KERNEL_SCALAR;
+    out->replicas_per_block = plan->RB;
+    out->blocks = (replicas + plan->RB - 1) / plan->RB;
+    if (plan->vec) {
+        out->threads = plan->NW * 32;
+        out->smem_bytes = (int64_t)hqa_vec_smem_bytes(ctx, plan->RB, plan->prec, plan->ent_bytes);
+    } else {
+        out->threads = std::min(32, std::max(1, plan->T)) * 32;
+        out->smem_bytes = (int64_t)hqa_sparse_smem_bytes(ctx, plan->RB, plan->prec);
+    }
+    out->pad_ratio = plan->pad_ratio;
+    out->conflict_ratio = plan->conflict_ratio;
+    out->balance = plan->vec ? plan->balance : 0.0;
+    return HQA_OK;
 }
 
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream)

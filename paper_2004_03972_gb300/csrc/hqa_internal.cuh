@@ -48,7 +48,23 @@ struct SparsePlan {
     int* d_tuple_rows = nullptr;  // [T][G] row index or -1
     double pad_ratio = 0.0;       // stored positions / nnz
     double conflict_ratio = 0.0;  // bank wavefronts / conflict-free wavefronts (host model)
+    // vectorised variant (sparse_md_vec.cu): 16-byte gathers, entries staged in shared memory
+    bool vec = false;
+    int NW = 0;                   // warps per CTA
+    int P = 0;                    // rows per bank phase
+    size_t ent_bytes = 0;         // packed u16 neighbour offsets (bytes)
+    int* d_slot_of_row = nullptr; // [N] shared-memory slot of each row (vectorised plan)
+    int* d_warp_off = nullptr;    // [NW + 1] offsets into d_tuple_list
+    int* d_tuple_list = nullptr;  // tuples in per-warp order
+    double balance = 0.0;         // mean warp load / max warp load
 };
+
+// Orders one section of G neighbour lists into K positions so that rows read
+// at one position fall in distinct bank groups (row j -> group j mod P, the
+// lists split into G / P phases of P rows) where possible; empty slots read
+// zero rows N .. N+P-1.  Adds the modelled wavefront count to `wavefronts`.
+void hqa_schedule_bank_section(const std::vector<std::vector<int>>& lists, int P, int N, int K,
+                               std::vector<int>& out /* [K][G] */, int64_t& wavefronts);
 
 struct hqa_ctx {
     int device = 0;
@@ -97,6 +113,17 @@ struct hqa_ctx {
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;
 // cudaFree synchronises the device, so in-flight users are finished).
 hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes);
+
+// sparse_md_vec.cu
+bool hqa_vec_supported(const hqa_ctx* ctx, int RB, int prec);
+size_t hqa_vec_smem_bytes(const hqa_ctx* ctx, int RB, int prec, size_t ent_bytes);
+hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out);
+hqa_status hqa_vec_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const StepCoef* d_sched,
+                             int64_t S, int32_t W, int32_t R, uint64_t seed, int init,
+                             const float* phi0, const float* p0, int M, float* phi_out,
+                             float* p_out, float* phibar_out, cudaStream_t st);
+hqa_status hqa_vec_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t R,
+                                const float* phi, float* L, cudaStream_t st);
 
 // sparse_md.cu
 hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out);

@@ -289,63 +289,65 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_field(const FieldArgs
 // host: plan construction
 // ---------------------------------------------------------------------------
 
-// Orders one section (G neighbour lists) into K positions so that the G
-// rows read at a position fall in distinct bank groups where possible.
-// Bank group of row j: j mod G.  Empty slots read one of the G zero rows
-// N..N+G-1 (chosen in a free group).
-static void schedule_section(const std::vector<std::vector<int>>& lists, int G, int N, int K,
-                             std::vector<int>& out /* [K][G] */, int64_t& wavefronts)
+}  // namespace
+
+void hqa_schedule_bank_section(const std::vector<std::vector<int>>& lists, int P, int N, int K,
+                               std::vector<int>& out /* [K][G] */, int64_t& wavefronts)
 {
+    const int G = (int)lists.size();
     out.assign((size_t)K * G, -1);
     // buckets[g][q] = rows of list g in bank group q
-    std::vector<std::vector<std::vector<int>>> bk(G, std::vector<std::vector<int>>(G));
+    std::vector<std::vector<std::vector<int>>> bk(G, std::vector<std::vector<int>>(P));
     std::vector<int> remaining(G, 0);
     for (int g = 0; g < G; ++g) {
-        for (int j : lists[g]) bk[g][j % G].push_back(j);
+        for (int j : lists[g]) bk[g][j % P].push_back(j);
         remaining[g] = (int)lists[g].size();
     }
-    std::vector<int> order(G);
-    std::vector<int> cnt(G);
+    std::vector<int> order(P);
+    std::vector<int> cnt(P);
     for (int pos = 0; pos < K; ++pos) {
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(),
-                  [&](int x, int y) { return remaining[x] > remaining[y]; });
-        uint64_t used = 0;
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (int g : order) {
-            int pick = -1;
-            if (remaining[g] > 0) {
-                int best_q = -1;
-                size_t best_n = 0;
-                for (int q = 0; q < G; ++q) {
-                    if ((used >> q) & 1ull) continue;
-                    if (bk[g][q].size() > best_n) { best_n = bk[g][q].size(); best_q = q; }
+        for (int ph = 0; ph < G / P; ++ph) {
+            for (int u = 0; u < P; ++u) order[u] = ph * P + u;
+            std::sort(order.begin(), order.end(),
+                      [&](int x, int y) { return remaining[x] > remaining[y]; });
+            uint64_t used = 0;
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (int g : order) {
+                int pick = -1;
+                if (remaining[g] > 0) {
+                    int best_q = -1;
+                    size_t best_n = 0;
+                    for (int q = 0; q < P; ++q) {
+                        if ((used >> q) & 1ull) continue;
+                        if (bk[g][q].size() > best_n) { best_n = bk[g][q].size(); best_q = q; }
+                    }
+                    if (best_q < 0)  // every non-empty group already used: accept a conflict
+                        for (int q = 0; q < P; ++q)
+                            if (!bk[g][q].empty() && (best_q < 0 || bk[g][q].size() > best_n)) {
+                                best_q = q;
+                                best_n = bk[g][q].size();
+                            }
+                    pick = bk[g][best_q].back();
+                    bk[g][best_q].pop_back();
+                    --remaining[g];
+                } else {
+                    int q = 0;
+                    while (q < P && ((used >> q) & 1ull)) ++q;
+                    if (q == P) q = 0;
+                    const int z = ((q - N % P) % P + P) % P;  // zero row N + z has group q
+                    pick = N + z;
                 }
-                if (best_q < 0)  // every non-empty group already used: accept a conflict
-                    for (int q = 0; q < G; ++q)
-                        if (!bk[g][q].empty() && (best_q < 0 || bk[g][q].size() > best_n)) {
-                            best_q = q;
-                            best_n = bk[g][q].size();
-                        }
-                pick = bk[g][best_q].back();
-                bk[g][best_q].pop_back();
-                --remaining[g];
-            } else {
-                int q = 0;
-                while (q < G && ((used >> q) & 1ull)) ++q;
-                if (q == G) q = 0;
-                const int z = ((q - N % G) % G + G) % G;  // zero row N + z has group q
-                pick = N + z;
+                const int q = pick % P;
+                used |= 1ull << q;
+                ++cnt[q];
+                out[(size_t)pos * G + g] = pick;
             }
-            const int q = pick % G;
-            used |= 1ull << q;
-            ++cnt[q];
-            out[(size_t)pos * G + g] = pick;
+            wavefronts += *std::max_element(cnt.begin(), cnt.end());
         }
-        wavefronts += *std::max_element(cnt.begin(), cnt.end());
     }
 }
 
+namespace {
 }  // namespace
 
 static size_t op_bytes(int Npad, int RB, int prec)
@@ -424,8 +426,8 @@ hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** ou
         }
         u.kp = (int)((mp + 3) / 4 * 4);
         u.kn = (int)((mn + 3) / 4 * 4);
-        schedule_section(lp, G, N, u.kp, u.pos, wave);
-        schedule_section(ln, G, N, u.kn, u.neg, wave);
+        hqa_schedule_bank_section(lp, G, N, u.kp, u.pos, wave);
+        hqa_schedule_bank_section(ln, G, N, u.kn, u.neg, wave);
         ideal += u.kp + u.kn;
         stored += (int64_t)(u.kp + u.kn) * G;
     }

@@ -24,12 +24,13 @@ STATUS_NAMES = {
 SCHED_PAPER, SCHED_LINEAR_GAMMA, SCHED_TABLE = 0, 1, 2
 INIT_PAPER, INIT_RANDOM_FLUX, INIT_GIVEN = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR = 0, 1, 2
 
 # every symbol include/hqa.h declares
 EXPORTS = (
     "hqa_schedule_default", "hqa_run_opts_default", "hqa_create_dense", "hqa_create_csr",
     "hqa_ctx_info", "hqa_run", "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
-    "hqa_solve_sub_noalloc", "hqa_sync", "hqa_status_string", "hqa_destroy",
+    "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync", "hqa_status_string", "hqa_destroy",
 )
 
 
@@ -61,6 +62,15 @@ class RunOpts(C.Structure):
         ("phi0", C.c_void_p),
         ("p0", C.c_void_p),
         ("replicas_per_block", C.c_int32),
+        ("kernel", C.c_int32),
+    ]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [
+        ("kernel", C.c_int32), ("replicas_per_block", C.c_int32), ("blocks", C.c_int32),
+        ("threads", C.c_int32), ("smem_bytes", C.c_int64), ("pad_ratio", C.c_double),
+        ("conflict_ratio", C.c_double), ("balance", C.c_double),
     ]
 
 
@@ -89,19 +99,20 @@ def lib() -> C.CDLL:
             L.hqa_ctx_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
             L.hqa_run.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i32, u64,
                                   C.POINTER(RunOpts), C.POINTER(Result), vp]
-            L.hqa_local_field.argtypes = [vp, i32, vp, vp, i32, vp]
+            L.hqa_local_field.argtypes = [vp, i32, vp, vp, C.POINTER(RunOpts), vp]
             L.hqa_readout.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
             L.hqa_energy.argtypes = [vp, i32, vp, vp, vp, vp]
             L.hqa_solve_sub.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
             L.hqa_solve_sub_noalloc.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
             L.hqa_sync.argtypes = [vp, vp]
+            L.hqa_plan_query.argtypes = [vp, i32, C.POINTER(RunOpts), C.POINTER(PlanInfo)]
             L.hqa_status_string.argtypes = [C.c_int]
             L.hqa_status_string.restype = C.c_char_p
             L.hqa_destroy.argtypes = [vp]
             L.hqa_destroy.restype = None
             for name in ("hqa_create_dense", "hqa_create_csr", "hqa_ctx_info", "hqa_run",
                          "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
-                         "hqa_solve_sub_noalloc", "hqa_sync"):
+                         "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -175,7 +186,7 @@ class Context:
 
     def run(self, steps, replicas, seed=0, sched=None, dt=None, precision=PREC_FP32,
             init=INIT_PAPER, phi0=None, p0=None, replicas_per_block=0, outputs=None,
-            out=None, stream=None, table=None):
+            out=None, stream=None, table=None, kernel=KERNEL_AUTO):
         """hqa_run. Returns a dict of device tensors (phi, p, phibar, spins, frozen, energy,
         cut, tally) -- those named in ``outputs`` (default: all), or the caller's ``out``."""
         import torch
@@ -196,6 +207,7 @@ class Context:
         opts.phi0 = None if phi0 is None else phi0.data_ptr()
         opts.p0 = None if p0 is None else p0.data_ptr()
         opts.replicas_per_block = replicas_per_block
+        opts.kernel = kernel
         if out is None:
             dev = torch.device("cuda")
             names = outputs or ("phi", "p", "phibar", "spins", "frozen", "energy", "cut", "tally")
@@ -211,11 +223,17 @@ class Context:
         del keep
         return out
 
-    def local_field(self, phi, precision=PREC_FP32, stream=None):
+    def local_field(self, phi, precision=PREC_FP32, replicas_per_block=0, kernel=KERNEL_AUTO,
+                    stream=None):
         import torch
         R = phi.shape[0]
         L = torch.empty_like(phi)
-        _check(lib().hqa_local_field(self._h, R, _ptr(phi), _ptr(L), precision,
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        opts.replicas_per_block = replicas_per_block
+        opts.kernel = kernel
+        _check(lib().hqa_local_field(self._h, R, _ptr(phi), _ptr(L), C.byref(opts),
                                      _stream_ptr(stream)), "hqa_local_field")
         return L
 
@@ -255,6 +273,18 @@ class Context:
                                            int(n), _ptr(out_spins), _ptr(out_energy),
                                            _stream_ptr(stream)), "hqa_solve_sub_noalloc")
         return out_spins, out_energy
+
+    def plan(self, replicas, precision=PREC_FP32, replicas_per_block=0, kernel=KERNEL_AUTO):
+        """hqa_plan_query: the launch plan hqa_run would use, as a dict."""
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        opts.replicas_per_block = replicas_per_block
+        opts.kernel = kernel
+        info = PlanInfo()
+        _check(lib().hqa_plan_query(self._h, int(replicas), C.byref(opts), C.byref(info)),
+               "hqa_plan_query")
+        return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
 
     def sync(self, stream=None):
         _check(lib().hqa_sync(self._h, _stream_ptr(stream)), "hqa_sync (latched device status)")

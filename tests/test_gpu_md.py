@@ -49,13 +49,22 @@ def _abs_scale(inst, phi):
 
 @pytest.mark.parametrize("name", ["er800", "sk100", "er_h", "reg3", "torus"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 1e-2)])
-@pytest.mark.parametrize("R", [1, 37])
-def test_local_field(hqa, orc, name, prec, tol, R):
+@pytest.mark.parametrize("R,rb,kernel", [(1, 0, 0), (37, 1, 1), (37, 8, 2), (45, 16, 2),
+                                         (70, 32, 2), (37, 4, 0)])
+def test_local_field(hqa, orc, name, prec, tol, R, rb, kernel):
     inst = _inst(name)
     ctx = hqa.Context.from_instance(inst)
     rng = np.random.default_rng(R)
     phi = rng.uniform(-1.5, 1.5, size=(R, inst.N)).astype(np.float32)
-    L = ctx.local_field(torch.from_numpy(phi).cuda(), precision=prec)
+    if kernel == hqa.KERNEL_VECTOR and rb < (8 if prec else 4):
+        pytest.skip("vector kernel needs a full 16-byte vector per lane")
+    try:
+        L = ctx.local_field(torch.from_numpy(phi).cuda(), precision=prec, replicas_per_block=rb,
+                            kernel=kernel)
+    except hqa.HQAError as e:
+        if e.status == 6 and kernel == hqa.KERNEL_VECTOR:
+            pytest.skip("vector kernel's shared-memory image does not fit at this blocking")
+        raise
     ctx.sync()
     L = L.cpu().numpy().astype(np.float64)
     pr = orc.Problem.from_instance(inst)
@@ -97,11 +106,13 @@ def _states_close(gpu, ref, tol, scale=None):
 
 @pytest.mark.parametrize("name", ["er800", "sk100", "er_h", "reg3"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 1e-2)])
-def test_states_after_100_steps(hqa, orc, name, prec, tol):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_states_after_100_steps(hqa, orc, name, prec, tol, kernel):
     inst = _inst(name)
     ctx = hqa.Context.from_instance(inst)
     R, S, seed, dt = 45, 100, 77, 1.0 / 5000
-    out = ctx.run(S, R, seed=seed, dt=dt, precision=prec, outputs=("phi", "p", "phibar"))
+    out = ctx.run(S, R, seed=seed, dt=dt, precision=prec, outputs=("phi", "p", "phibar"),
+                  kernel=kernel, replicas_per_block=8)
     ctx.sync()
     pr = orc.Problem.from_instance(inst)
     phi, p, pbar = (out[k].cpu().numpy().astype(np.float64) for k in ("phi", "p", "phibar"))
@@ -113,21 +124,25 @@ def test_states_after_100_steps(hqa, orc, name, prec, tol):
         assert _states_close(pbar[r], opbar, tol, scale=np.max(np.abs(ophi)))
 
 
-@pytest.mark.parametrize("rb", [1, 2, 4, 8, 16, 32])
-def test_every_replica_blocking_matches(hqa, orc, rb):
-    """Same run with each replicas-per-block choice (covers ragged last blocks)."""
+@pytest.mark.parametrize("rb,kernel,prec", [(1, 1, 0), (2, 1, 0), (4, 1, 0), (8, 1, 0), (16, 1, 0),
+                                            (32, 1, 0), (4, 2, 0), (8, 2, 0), (16, 2, 0),
+                                            (32, 2, 0), (8, 2, 1), (16, 2, 1), (32, 2, 1)])
+def test_every_replica_blocking_matches(hqa, orc, rb, kernel, prec):
+    """Same run with each replicas-per-block choice and kernel variant (covers ragged
+    last blocks)."""
     inst = _inst("er_h")
     ctx = hqa.Context.from_instance(inst)
     R, S, dt = 21, 60, 1.0 / 700
     out = ctx.run(S, R, seed=5, dt=dt, replicas_per_block=rb, init=hqa.INIT_RANDOM_FLUX,
-                  outputs=("phi", "p"))
+                  outputs=("phi", "p"), kernel=kernel, precision=prec)
+    tol = 1e-5 if prec == 0 else 1e-2
     ctx.sync()
     pr = orc.Problem.from_instance(inst)
     for r in (0, R - 1):
         ophi, op, _ = orc.md_run(pr, S, dt=dt, p0=orc.initial_momenta(5, r, inst.N),
                                  phi0=orc.initial_flux_random(5, r, inst.N))
-        assert _states_close(out["phi"][r].cpu().numpy(), ophi, 1e-5)
-        assert _states_close(out["p"][r].cpu().numpy(), op, 1e-5, scale=1.0)
+        assert _states_close(out["phi"][r].cpu().numpy(), ophi, tol)
+        assert _states_close(out["p"][r].cpu().numpy(), op, tol, scale=1.0)
 
 
 def test_linear_gamma_and_table_schedules(hqa, orc):
@@ -160,7 +175,8 @@ def test_potential_exponents(hqa, orc):
         assert _states_close(out["phi"][1].cpu().numpy(), ophi, 1e-5)
 
 
-def test_z2_symmetry_bitwise(hqa):
+@pytest.mark.parametrize("kernel,prec", [(1, 0), (2, 0), (2, 1)])
+def test_z2_symmetry_bitwise(hqa, kernel, prec):
     """h = 0: negating p(0) negates the whole trajectory exactly (odd-symmetric rounding)."""
     inst = _inst("er800")
     ctx = hqa.Context.from_instance(inst)
@@ -168,8 +184,10 @@ def test_z2_symmetry_bitwise(hqa):
     g = torch.Generator().manual_seed(0)
     p0 = (torch.randint(0, 2, (R, inst.N), generator=g) * 2 - 1).float().cuda()
     phi0 = torch.zeros(R, inst.N, device="cuda")
-    a = ctx.run(S, R, init=hqa.INIT_GIVEN, phi0=phi0, p0=p0, outputs=("phi", "p", "phibar"))
-    b = ctx.run(S, R, init=hqa.INIT_GIVEN, phi0=phi0, p0=-p0, outputs=("phi", "p", "phibar"))
+    kw = dict(init=hqa.INIT_GIVEN, phi0=phi0, outputs=("phi", "p", "phibar"), kernel=kernel,
+              precision=prec, replicas_per_block=8)
+    a = ctx.run(S, R, p0=p0, **kw)
+    b = ctx.run(S, R, p0=-p0, **kw)
     ctx.sync()
     for k in ("phi", "p", "phibar"):
         assert torch.equal(a[k], -b[k])
