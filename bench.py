@@ -141,6 +141,17 @@ def ncu_traffic(kernel_key):
     return ent["dram_bytes_per_launch"]
 
 
+def median_diff_ci(a, b, reps=2000, seed=0):
+    """Bootstrap 95% interval of median(a) - median(b)."""
+    rng = np.random.default_rng(seed)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    ma = np.median(rng.choice(a, size=(reps, a.size), replace=True), axis=1)
+    mb = np.median(rng.choice(b, size=(reps, b.size), replace=True), axis=1)
+    lo, hi = np.percentile(ma - mb, [2.5, 97.5])
+    return float(lo), float(hi)
+
+
 def bootstrap_halfwidth(x, reps=2000, seed=0):
     rng = np.random.default_rng(seed)
     x = np.asarray(x, np.float64)
@@ -226,7 +237,7 @@ def run_ours(args):
             def md_only(k, prec=prec):
                 ctx.run(S, R, seed=seed_base + k, sched=sched, precision=prec, out=md_out)
             t_md = timed(md_only, args.steps, 1)
-            variants[name] = dict(prec=prec, t_pipe=t_pipe, t_md=t_md,
+            variants[name] = dict(prec=prec, t_pipe=t_pipe, t_md=t_md, cuts=allcuts,
                                   median_cut=float(np.median(allcuts)),
                                   cut_ci95_halfwidth=bootstrap_halfwidth(allcuts),
                                   mean_cut=float(np.mean(allcuts)))
@@ -253,7 +264,9 @@ def run_ours(args):
             host_c.copy_(out["cut"], non_blocking=True)
 
         fp, bf = variants["fp32"], variants["bf16"]
-        equal_cut = bf["median_cut"] >= fp["median_cut"] - fp["cut_ci95_halfwidth"]
+        # equal cut: the 95% interval of median(bf16) - median(fp32) reaches 0 or above
+        diff_lo, diff_hi = median_diff_ci(bf["cuts"], fp["cuts"])
+        equal_cut = diff_hi >= 0.0
         head = "bf16" if (equal_cut and np.mean(bf["t_pipe"]) < np.mean(fp["t_pipe"])) else "fp32"
         best_prec = variants[head]["prec"]
         t_e2e = timed(e2e_step, args.steps, args.warmup)
@@ -302,6 +315,8 @@ def run_ours(args):
                          "median_cut": v["median_cut"], "cut_ci95_halfwidth": v["cut_ci95_halfwidth"],
                          "mean_cut": v["mean_cut"]} for k, v in variants.items()},
         "headline_variant": head,
+        "equal_cut": {"rule": "95% bootstrap interval of median(bf16 cut) - median(fp32 cut) reaches 0",
+                      "interval": [diff_lo, diff_hi], "holds": bool(equal_cut)},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s",
                 "h2d_bytes_per_step": 2 * R * N * 4, "d2h_bytes_per_step": R * N + 2 * R * 8},
         "gpu_launches": launches_per_step * args.steps,

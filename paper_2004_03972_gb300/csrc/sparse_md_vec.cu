@@ -114,6 +114,43 @@ struct Gather {
 // lane's first uint4 of entries (8 u16 offsets), consecutive chunks G * 16
 // bytes apart; nhalf: number of 4-position half-chunks; base: shared address
 // of this lane's quad in the current operand buffer.
+// acc[0..1] += bf16 pair in w (lo -> acc0, hi -> acc1): Blackwell's mixed
+// add converts the BF16 operand and adds it to the FP32 sum in one instruction.
+__device__ __forceinline__ void add_bf16x2(float& a0, float& a1, uint32_t w)
+{
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
+        : "+f"(a0), "+f"(a1) : "r"(w));
+}
+
+// BF16 operand: 8 FP32 accumulators, one per replica of the lane.
+template <int G>
+__device__ __forceinline__ void tuple_field_bf16(uint32_t ent, int nhalf, uint32_t base, float* acc)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    for (int hc = 0; hc < nhalf; hc += 2) {
+        const uint4 e = lds128(ent + (uint32_t)(hc >> 1) * (G * 16u));
+        const uint32_t ew[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && hc + 1 >= nhalf) break;
+            uint4 v[4];
+            v[0] = lds128(base + ((ew[2 * h] & 0xffffu) << 4));
+            v[1] = lds128(base + ((ew[2 * h] >> 16) << 4));
+            v[2] = lds128(base + ((ew[2 * h + 1] & 0xffffu) << 4));
+            v[3] = lds128(base + ((ew[2 * h + 1] >> 16) << 4));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                add_bf16x2(acc[0], acc[1], v[u].x);
+                add_bf16x2(acc[2], acc[3], v[u].y);
+                add_bf16x2(acc[4], acc[5], v[u].z);
+                add_bf16x2(acc[6], acc[7], v[u].w);
+            }
+        }
+    }
+}
+
 template <int G, bool BF16>
 __device__ __forceinline__ void tuple_field_vec(uint32_t ent, int nhalf, uint32_t base,
                                                 uint64_t* acc)
@@ -237,9 +274,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md_vec(const VArgs a)
         for (int k = wbeg; k < wend; ++k) {
             const int t = __ldg(a.tuple_list + k);
             const int4 tp = __ldg(a.tuples + t);
-            uint64_t acc[NP];
-            tuple_field_vec<G, BF16>(s0 + ((uint32_t)tp.x * G + g) * 16u, tp.y,
-                                     cur + (uint32_t)q * 16u, acc);
+            float Lsum[V];
+            if constexpr (BF16) {
+                tuple_field_bf16<G>(s0 + ((uint32_t)tp.x * G + g) * 16u, tp.y,
+                                    cur + (uint32_t)q * 16u, Lsum);
+            } else {
+                uint64_t acc[NP];
+                tuple_field_vec<G, BF16>(s0 + ((uint32_t)tp.x * G + g) * 16u, tp.y,
+                                         cur + (uint32_t)q * 16u, acc);
+#pragma unroll
+                for (int u = 0; u < V; ++u) Lsum[u] = (u & 1) ? hi_f(acc[u >> 1]) : lo_f(acc[u >> 1]);
+            }
             const int row = __ldg(a.tuple_rows + t * G + g);
             if (row < 0) continue;
             const uint32_t e0 = (uint32_t)(__ldg(a.slot_of_row + row) * RB + q * V);
@@ -257,8 +302,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md_vec(const VArgs a)
             }
 #pragma unroll
             for (int u = 0; u < V; ++u) {
-                float L = (u & 1) ? hi_f(acc[u >> 1]) : lo_f(acc[u >> 1]);
-                L += hr * fabsf(phi[u]);
+                const float L = Lsum[u] + hr * fabsf(phi[u]);
                 const float phi2 = phi[u] * phi[u];
                 float pw = phi[u];
                 for (int m = 0; m < mhalf; ++m) pw *= phi2;
@@ -364,16 +408,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_field_vec(const VArgs
     for (int k = wbeg; k < wend; ++k) {
         const int t = __ldg(a.tuple_list + k);
         const int4 tp = __ldg(a.tuples + t);
-        uint64_t acc[NP];
-        tuple_field_vec<G, BF16>(s0 + ((uint32_t)tp.x * G + g) * 16u, tp.y,
-                                 op0 + (uint32_t)q * 16u, acc);
+        float Lsum[V];
+        if constexpr (BF16) {
+            tuple_field_bf16<G>(s0 + ((uint32_t)tp.x * G + g) * 16u, tp.y, op0 + (uint32_t)q * 16u,
+                                Lsum);
+        } else {
+            uint64_t acc[NP];
+            tuple_field_vec<G, BF16>(s0 + ((uint32_t)tp.x * G + g) * 16u, tp.y,
+                                     op0 + (uint32_t)q * 16u, acc);
+#pragma unroll
+            for (int u = 0; u < V; ++u) Lsum[u] = (u & 1) ? hi_f(acc[u >> 1]) : lo_f(acc[u >> 1]);
+        }
         const int row = __ldg(a.tuple_rows + t * G + g);
         if (row < 0) continue;
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int rep = rep0 + q * V + u;
             if (rep >= a.R) continue;
-            float L = (u & 1) ? hi_f(acc[u >> 1]) : lo_f(acc[u >> 1]);
+            float L = Lsum[u];
             if (a.h) L += 2.f * __ldg(a.h + row) * fabsf(a.phi_in[(size_t)rep * a.N + row]);
             a.L_out[(size_t)rep * a.N + row] = L;
         }
