@@ -1,20 +1,26 @@
 #!/usr/bin/env python3
 """HQA-MD benchmark: flux-MD spin-updates/s on one GB300.
 
-Workload (default, --config er800): Erdos-Renyi G(800, 0.06) with +-1 weights
-in CSR, 1024 replicas with seeded +-1 initial momenta, 5000 leapfrog steps of
-the paper's schedule (dt = 1/5000), then readout, int64 energy/cut and the
-exact sub-solve of the n = 24 least-frozen spins per replica.  One bench
-"step" is that whole pipeline over the 1024 replicas.  Spin-updates per step
-= N * R * S (one leapfrog step of one spin in one replica).
+Workloads (--config):
+  er800  (default) Erdos-Renyi G(800, 0.06) with +-1 weights in CSR, 1024
+         replicas with seeded +-1 initial momenta, 5000 leapfrog steps of the
+         paper's schedule (dt = 1/5000).  Variants: plain FP32 operand and BF16
+         operand (FP32 accumulate, FP32 state) on the resident sparse kernel.
+  sk2000 SK / K2000 with +-1 weights (dense), 4096 replicas, 10000 steps.
+         Variants on the tcgen05 dense kernel: split BF16 operand (hi + lo,
+         ~16 significant bits: the FP32-accurate reference variant) and plain
+         BF16 operand.
+  sk100  SK N = 100, 1 replica, 1000 steps, linear-Gamma schedule (latency).
+One bench "step" is the whole pipeline over all replicas: MD, readout,
+int64 energy/cut and the exact sub-solve of the n least-frozen spins.
+Spin-updates per step = N * R * S (one leapfrog step of one spin in one replica).
 
-Variants: plain FP32 operand and BF16 operand (FP32 accumulate, FP32 state).
-The headline value is the faster variant whose median cut is not below the
-plain variant's median cut minus its bootstrap 95% half-width (equal-cut
-rule); both are reported under "variants".
+The headline value is the fastest variant whose median cut is not worse than
+the plain variant's (the 95% bootstrap interval of the median difference
+reaches 0); every variant is reported under "variants".
 
 The reference arm (--impl reference) times the FP64 CPU oracle on the host
-cores over a bounded sample of the same workload.
+cores over a bounded sample of the same workload (the paper has no code).
 """
 from __future__ import annotations
 
@@ -33,19 +39,34 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "flux-MD spin-updates/s on 1 GB300, mixed/batched vs plain FP32 at equal cut"
+
 CONFIGS = {
-    # name: (builder, N-ish label, replicas, steps, n_ambivalent)
-    "er800": dict(desc="ER G(800,0.06) +-1 CSR, 1024 replicas, 5000 steps, paper schedule, n=24 exact sub-solve",
-                  R=1024, S=5000, n=24),
-    "sk100": dict(desc="SK N=100 +-1, 1 replica, 1000 steps, linear-gamma schedule, n=20 exact sub-solve",
-                  R=1, S=1000, n=20),
+    "er800": dict(desc="ER G(800,0.06) +-1 CSR, 1024 replicas, 5000 steps, paper schedule, "
+                       "n=24 exact sub-solve",
+                  R=1024, S=5000, n=24, kind="sparse", sched="paper",
+                  variants=(("fp32", "PREC_FP32"), ("bf16", "PREC_BF16")), plain="fp32",
+                  cpu_steps=None),
+    "sk2000": dict(desc="SK K2000 +-1 dense, 4096 replicas, 10000 steps, paper schedule, "
+                        "n=24 exact sub-solve, tcgen05 field",
+                   R=4096, S=10000, n=24, kind="dense", sched="paper",
+                   variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
+                   cpu_steps=200),
+    "sk100": dict(desc="SK N=100 +-1, 1 replica, 1000 steps, linear-gamma schedule, "
+                       "n=20 exact sub-solve",
+                  R=1, S=1000, n=20, kind="sparse", sched="linear_gamma",
+                  variants=(("fp32", "PREC_FP32"),), plain="fp32", cpu_steps=None),
 }
+
+ELEM_BYTES = {"PREC_FP32": 4, "PREC_BF16": 2, "PREC_BF16X2": 4}
 
 
 def make_instance(name):
     from paper_2004_03972_gb300 import instances
     if name == "er800":
         return instances.er_pm1(800, 0.06, 1200)
+    if name == "sk2000":
+        return instances.sk_pm1(2000, 1300)
     if name == "sk100":
         return instances.sk_pm1(100, 1100)
     raise KeyError(name)
@@ -113,11 +134,14 @@ class ClockSampler:
 
 
 def measured_peaks():
+    """Tensor peak (TFLOP/s) for a seconds-long kernel: the driver's sustained figure."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            return json.load(f), "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+            d = json.load(f)
+        t = d.get("bf16_tflops_sustained") or d.get("bf16_tflops")
+        return {"bf16_tflops": float(t), "hbm_gbs": d.get("hbm_gbs"), "source": "of measured"}
+    return {"bf16_tflops": 1700.0, "hbm_gbs": 6800.0, "source": "of fallback (sustained)"}
 
 
 def _src_sha(path):
@@ -160,6 +184,15 @@ def bootstrap_halfwidth(x, reps=2000, seed=0):
     return float(hi - lo) / 2
 
 
+def kernel_name(hqa, plan, prec_name):
+    k = plan["kernel"]
+    if k == hqa.KERNEL_DENSE:
+        split = "true" if prec_name == "PREC_BF16X2" else "false"
+        return f"k_dense_md<{plan['replicas_per_block'] // 2},4,{split}>"
+    base = "k_sparse_md_vec" if k == hqa.KERNEL_VECTOR else "k_sparse_md"
+    return f"{base}<{plan['replicas_per_block']},{'true' if prec_name == 'PREC_BF16' else 'false'}>"
+
+
 def run_ours(args):
     import torch
 
@@ -175,12 +208,11 @@ def run_ours(args):
     N, R, S, n = inst.N, cfg["R"], cfg["S"], cfg["n"]
     ctx = hqa.Context.from_instance(inst)
     sched = hqa.schedule(n_ambivalent=n)
-    if args.config == "sk100":
+    if cfg["sched"] == "linear_gamma":
         sched.kind = hqa.SCHED_LINEAR_GAMMA
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
-    launches_per_step = 1 + 1 + 1 + 4   # md, readout, energy, sub-solve (prep, enum, assemble, energy)
     seed_base = 1000 + rank * 100003
 
     out = {k: torch.empty(s, dtype=d, device=dev) for k, s, d in (
@@ -191,8 +223,7 @@ def run_ours(args):
 
     def pipeline(prec, seed):
         ctx.run(S, R, seed=seed, sched=sched, precision=prec, out=out)
-        sub_s, sub_e = ctx.solve_sub(out["spins"], out["frozen"], n)
-        return sub_s, sub_e
+        return ctx.solve_sub(out["spins"], out["frozen"], n)
 
     def timed(fn, K, W):
         for w in range(W):
@@ -218,29 +249,33 @@ def run_ours(args):
     variants = {}
     clocks = ClockSampler(local)
     with clocks:
-        for name, prec in (("fp32", hqa.PREC_FP32), ("bf16", hqa.PREC_BF16)):
-            cuts = []
-
-            def step(k, prec=prec, cuts=cuts):
-                pipeline(prec, seed_base + k)
-            t_pipe = timed(step, args.steps, args.warmup)
+        for name, prec_name in cfg["variants"]:
+            prec = getattr(hqa, prec_name)
+            t_pipe = timed(lambda k, prec=prec: pipeline(prec, seed_base + k), args.steps, args.warmup)
             ctx.sync()
-            # quality at equal cut: MD readout cuts over the same seeds for both variants
+            # quality: MD readout cuts over the same seeds for every variant
+            cuts = []
             for k in range(args.steps):
                 ctx.run(S, R, seed=seed_base + 7 * k, sched=sched, precision=prec, out=out)
                 cuts.append(out["cut"].cpu().numpy().copy())
             ctx.sync()
             allcuts = np.concatenate(cuts)
-            # MD kernel alone (roofline)
-            md_out = {"phibar": out["phibar"]}
-
-            def md_only(k, prec=prec):
-                ctx.run(S, R, seed=seed_base + k, sched=sched, precision=prec, out=md_out)
-            t_md = timed(md_only, args.steps, 1)
-            variants[name] = dict(prec=prec, t_pipe=t_pipe, t_md=t_md, cuts=allcuts,
-                                  median_cut=float(np.median(allcuts)),
+            md_out = {"phibar": out["phibar"]}   # MD kernel alone (roofline timing)
+            t_md = timed(lambda k, prec=prec: ctx.run(S, R, seed=seed_base + k, sched=sched,
+                                                      precision=prec, out=md_out), args.steps, 1)
+            variants[name] = dict(prec=prec, prec_name=prec_name, t_pipe=t_pipe, t_md=t_md,
+                                  cuts=allcuts, median_cut=float(np.median(allcuts)),
                                   cut_ci95_halfwidth=bootstrap_halfwidth(allcuts),
                                   mean_cut=float(np.mean(allcuts)))
+        # headline: fastest variant at equal cut with the plain one
+        plain = variants[cfg["plain"]]
+        eq = {}
+        for name, v in variants.items():
+            lo, hi = median_diff_ci(v["cuts"], plain["cuts"]) if name != cfg["plain"] else (0.0, 0.0)
+            eq[name] = {"interval": [lo, hi], "holds": hi >= 0.0}
+        head = min((k for k in variants if eq[k]["holds"]),
+                   key=lambda k: np.mean(variants[k]["t_pipe"]))
+        best_prec = variants[head]["prec"]
         # end-to-end through the public API with host buffers
         pin_p0 = torch.empty((R, N), dtype=torch.float32).pin_memory()
         pin_phi0 = torch.zeros((R, N), dtype=torch.float32).pin_memory()
@@ -251,7 +286,6 @@ def run_ours(args):
         host_c = torch.empty((R,), dtype=torch.int64).pin_memory()
         d_p0 = torch.empty((R, N), dtype=torch.float32, device=dev)
         d_phi0 = torch.empty((R, N), dtype=torch.float32, device=dev)
-        best_prec = hqa.PREC_FP32
 
         def e2e_step(k):
             d_p0.copy_(pin_p0, non_blocking=True)
@@ -263,12 +297,6 @@ def run_ours(args):
             host_e.copy_(sub_e, non_blocking=True)
             host_c.copy_(out["cut"], non_blocking=True)
 
-        fp, bf = variants["fp32"], variants["bf16"]
-        # equal cut: the 95% interval of median(bf16) - median(fp32) reaches 0 or above
-        diff_lo, diff_hi = median_diff_ci(bf["cuts"], fp["cuts"])
-        equal_cut = diff_hi >= 0.0
-        head = "bf16" if (equal_cut and np.mean(bf["t_pipe"]) < np.mean(fp["t_pipe"])) else "fp32"
-        best_prec = variants[head]["prec"]
         t_e2e = timed(e2e_step, args.steps, args.warmup)
     ctx.sync()
 
@@ -283,47 +311,61 @@ def run_ours(args):
     value = su_step * args.steps * ws / tot_pipe
     e2e_value = su_step * args.steps * ws / tot_e2e
 
-    # roofline of the dominant kernel (the resident sparse MD kernel)
+    # roofline of the dominant kernel (the MD kernel), timed alone with CUDA events
     clk = clocks.summary()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    es = 2 if head == "bf16" else 4
-    nnz = inst.nnz
-    bytes_per_launch = nnz * es * R * S     # gathered operand bytes: deg x elem size per spin-update
-    t_md = float(np.mean(variants[head]["t_md"]))
-    achieved = bytes_per_launch / t_md / 1e9
-    mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_smem = sm_count * 128 * mhz * 1e6 / 1e9    # GB/s: 128 B/clk/SM shared-memory bandwidth
-    plan = ctx.plan(R, precision=variants[head]["prec"])
-    rb = plan["replicas_per_block"]
-    kname = ("k_sparse_md_vec" if plan["kernel"] == hqa.KERNEL_VECTOR else "k_sparse_md") + \
-        f"<{rb},{'true' if head == 'bf16' else 'false'}>"
-    traffic = ncu_traffic(f"{kname}@{args.config}")
+    hv = variants[head]
+    plan = ctx.plan(R, precision=hv["prec"])
+    kname = kernel_name(hqa, plan, hv["prec_name"])
+    t_md = float(np.mean(hv["t_md"]))
+    if cfg["kind"] == "dense":
+        pk = measured_peaks()
+        flops = 2.0 * N * N * R * S                     # algorithmic: the field GEMM
+        mma = flops * (2 if hv["prec_name"] == "PREC_BF16X2" else 1)
+        achieved = flops / t_md / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
+                "mma_tflops_issued": mma / t_md / 1e12, "peak_source": pk["source"]}
+    else:
+        es = ELEM_BYTES[hv["prec_name"]]
+        bytes_per_launch = inst.nnz * es * R * S   # gathered operand bytes: deg x elem size per spin-update
+        achieved = bytes_per_launch / t_md / 1e9
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_max_mhz") or 2070.0
+        peak = sm_count * 128 * mhz * 1e6 / 1e9     # GB/s: 128 B/clk/SM shared-memory bandwidth
+        roof = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "peak_source": "derived: SMs x 128 B/clk x max SM clock (shared-memory bandwidth)"}
+    roof["traffic"] = ncu_traffic(f"{kname}@{args.config}")
+    roof["kernel"] = kname
+    roof["kernel_ms"] = 1e3 * t_md
+    roof["plan"] = plan
 
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
+    # launches per pipeline step: MD (+ init and output copy on the dense path),
+    # readout, energy, sub-solve (prep, enumeration, assemble, energy)
+    launches = (3 if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + 4
     line = {
-        "metric": "flux-MD spin-updates/s on 1 GB300, mixed/batched vs plain FP32 at equal cut",
-        "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * tot_pipe / args.steps,
+        "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_pipe / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if head == "fp32" else "bf16-operand/f32-accumulate",
+        "dtype": {"PREC_FP32": "f32", "PREC_BF16": "bf16-operand/f32-accumulate",
+                  "PREC_BF16X2": "bf16x2-split-operand/f32-accumulate"}[hv["prec_name"]],
         "data": "synthetic (seeded instance generator)",
-        "config": {"workload": cfg["desc"], "N": N, "nnz": nnz, "replicas": R, "md_steps": S,
+        "config": {"workload": cfg["desc"], "N": N, "nnz": inst.nnz, "replicas": R, "md_steps": S,
                    "n_ambivalent": n, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas only, {ws} GPU(s)"},
         "variants": {k: {"spin_updates_per_s": su_step * args.steps / sum(v["t_pipe"]),
                          "md_kernel_ms": 1e3 * float(np.mean(v["t_md"])),
                          "median_cut": v["median_cut"], "cut_ci95_halfwidth": v["cut_ci95_halfwidth"],
-                         "mean_cut": v["mean_cut"]} for k, v in variants.items()},
+                         "mean_cut": v["mean_cut"], "equal_cut_vs_plain": eq[k]}
+                     for k, v in variants.items()},
         "headline_variant": head,
-        "equal_cut": {"rule": "95% bootstrap interval of median(bf16 cut) - median(fp32 cut) reaches 0",
-                      "interval": [diff_lo, diff_hi], "holds": bool(equal_cut)},
+        "equal_cut": {"rule": "95% bootstrap interval of median(variant cut) - median(plain cut) "
+                              "reaches 0", "plain": cfg["plain"]},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s",
                 "h2d_bytes_per_step": 2 * R * N * 4, "d2h_bytes_per_step": R * N + 2 * R * 8},
-        "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "smem", "achieved": achieved, "peak": peak_smem, "unit": "GB/s",
-                     "frac": achieved / peak_smem, "traffic": traffic,
-                     "kernel": kname, "plan": plan,
-                     "peak_source": "derived: SMs x 128 B/clk x max SM clock (shared-memory bandwidth)"},
+        "gpu_launches": launches * args.steps,
+        "roofline": roof,
         "clocks": clk,
     }
     if cpu:
@@ -334,10 +376,10 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def _oracle_sample(inst, cfg, reps, threads):
+def _oracle_sample(inst, S, reps, threads):
     from oracle import oracle as orc
     pr = orc.Problem.from_instance(inst)
-    N, S = inst.N, cfg["S"]
+    N = inst.N
     p0 = np.stack([orc.initial_momenta(9, r, N) for r in range(reps)])
     phi0 = np.zeros_like(p0)
     t0 = time.perf_counter()
@@ -345,15 +387,22 @@ def _oracle_sample(inst, cfg, reps, threads):
     return time.perf_counter() - t0
 
 
+def _cpu_sample_shape(cfg, cores, scale):
+    S = cfg["cpu_steps"] or cfg["S"]
+    reps = max(1, min(cfg["R"], scale * cores))
+    return S, reps
+
+
 def cpu_baseline(args, inst, cfg):
     from oracle import oracle as orc
     orc.build()
     cores = os.cpu_count() or 1
-    reps = max(1, min(cfg["R"], 16 * cores))
-    wall = _oracle_sample(inst, cfg, reps, cores)
-    return {"value": inst.N * reps * cfg["S"] / wall, "unit": "spin-updates/s", "cores": cores,
+    S, reps = _cpu_sample_shape(cfg, cores, 16 if cfg["kind"] == "sparse" else 2)
+    wall = _oracle_sample(inst, S, reps, cores)
+    return {"value": inst.N * reps * S / wall, "unit": "spin-updates/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"{reps} of {cfg['R']} replicas x {cfg['S']} steps (MD only, FP64, OpenMP over replicas)"}
+            "sample": f"{reps} of {cfg['R']} replicas x {S} of {cfg['S']} steps "
+                      "(MD only, FP64, OpenMP over replicas)"}
 
 
 def run_reference(args):
@@ -365,18 +414,17 @@ def run_reference(args):
     cfg = CONFIGS[args.config]
     inst = make_instance(args.config)
     cores = os.cpu_count() or 1
-    reps = max(1, min(cfg["R"], cores))
+    S, reps = _cpu_sample_shape(cfg, cores, 1)
     for _ in range(args.warmup):
-        _oracle_sample(inst, dict(cfg, S=50), reps, cores)
-    walls = [_oracle_sample(inst, cfg, reps, cores) for _ in range(args.steps)]
-    value = inst.N * reps * cfg["S"] * args.steps / sum(walls)
-    sample = f"{reps} of {cfg['R']} replicas x {cfg['S']} steps per step (MD only, FP64 oracle)"
+        _oracle_sample(inst, min(S, 20), reps, cores)
+    walls = [_oracle_sample(inst, S, reps, cores) for _ in range(args.steps)]
+    value = inst.N * reps * S * args.steps / sum(walls)
+    sample = f"{reps} of {cfg['R']} replicas x {S} of {cfg['S']} steps per step (MD only, FP64 oracle)"
     print(json.dumps({
-        "impl": "reference",
-        "metric": "flux-MD spin-updates/s on 1 GB300, mixed/batched vs plain FP32 at equal cut",
-        "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded instance generator)",
         "config": {"workload": cfg["desc"], "N": inst.N, "replicas": cfg["R"], "md_steps": cfg["S"]},
         "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",

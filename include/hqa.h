@@ -85,16 +85,20 @@ enum {
 
 /* Arithmetic of the local-field operand. */
 enum {
-    HQA_PREC_FP32 = 0, /* phi operand FP32, FP32 accumulate */
-    HQA_PREC_BF16 = 1  /* phi operand rounded to BF16, FP32 accumulate; phi, p stay FP32 */
+    HQA_PREC_FP32 = 0,  /* phi operand FP32, FP32 accumulate */
+    HQA_PREC_BF16 = 1,  /* phi operand rounded to BF16, FP32 accumulate; phi, p stay FP32 */
+    HQA_PREC_BF16X2 = 2 /* dense tensor-core path only: phi = hi + lo, both BF16 (about 16
+                           significant bits), two MMAs per k-step, FP32 accumulate */
 };
 
 /* Sparse kernel variants (both compute the same sums, in different orders). */
 enum {
     HQA_KERNEL_AUTO = 0,   /* vectorised when the blocking allows, else scalar */
     HQA_KERNEL_SCALAR = 1, /* one replica per lane, neighbour lists streamed from L1/L2 */
-    HQA_KERNEL_VECTOR = 2  /* 16-byte gathers per lane, lists in shared memory; needs
+    HQA_KERNEL_VECTOR = 2, /* 16-byte gathers per lane, lists in shared memory; needs
                               replicas_per_block >= 4 (FP32) or >= 8 (BF16) */
+    HQA_KERNEL_DENSE = 3   /* tcgen05 tensor-core GEMM; dense contexts whose couplings
+                              are exact in BF16, BF16 operand only */
 };
 
 typedef struct {

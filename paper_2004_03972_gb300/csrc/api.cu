@@ -40,8 +40,8 @@ void free_ctx_device(hqa_ctx* c)
         if (kv.second.d_tuple_list) cudaFree(kv.second.d_tuple_list);
     }
     c->plans.clear();
-    void* ptrs[] = {c->d_row_ptr, c->d_col,  c->d_val, c->d_val_i8, c->d_h,     c->d_h_i32,
-                    c->d_sched,   c->d_ws,   c->d_state, c->d_sub,  c->d_status};
+    void* ptrs[] = {c->d_row_ptr, c->d_col, c->d_val,   c->d_val_i8, c->d_h,      c->d_h_i32,
+                    c->d_sched,   c->d_ws,  c->d_state, c->d_sub,    c->d_status, c->d_Jbf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -195,11 +195,13 @@ hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t
 
 hqa_status check_opts(const hqa_run_opts& o)
 {
-    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16) return HQA_ERR_INVALID_ARG;
+    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16 &&
+        o.precision != HQA_PREC_BF16X2)
+        return HQA_ERR_INVALID_ARG;
     const int rbq = o.replicas_per_block;
     if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
         return HQA_ERR_INVALID_ARG;
-    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_VECTOR) return HQA_ERR_INVALID_ARG;
+    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_DENSE) return HQA_ERR_INVALID_ARG;
     return HQA_OK;
 }
 
@@ -343,7 +345,14 @@ hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t 
         c->row_ptr[i + 1] = (int64_t)c->col.size();
     }
     if (h) c->h.assign(h, h + N);
-    return create_guarded(c, out);
+    hqa_status s = create_guarded(c, out);
+    if (s != HQA_OK) return s;
+    s = hqa_dense_setup(c, J);
+    if (s != HQA_OK) {
+        hqa_destroy(c);
+        *out = nullptr;
+    }
+    return s;
 }
 
 hqa_status hqa_ctx_info(const hqa_ctx* ctx, int32_t* N, int64_t* nnz, int32_t* integer_couplings)
@@ -376,12 +385,19 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     const bool want_readout = out->spins || out->frozen || out->tally || out->energy || out->cut;
     const bool want_energy = out->energy || out->cut;
     if (want_energy && !ctx->integer) return HQA_ERR_UNSUPPORTED;
-    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // dense tensor-core path: dense contexts exact in BF16, BF16 operand
+    const bool tc_prec = o.precision == HQA_PREC_BF16 || o.precision == HQA_PREC_BF16X2;
+    const bool dense = o.kernel == HQA_KERNEL_DENSE ||
+                       (o.kernel == HQA_KERNEL_AUTO && tc_prec && hqa_dense_md_possible(ctx, replicas));
+    if (dense && (!ctx->dense_tc || !tc_prec)) return HQA_ERR_UNSUPPORTED;
+    if (!dense && (!ctx->unit || o.precision == HQA_PREC_BF16X2)) return HQA_ERR_UNSUPPORTED;
 
     const SparsePlan* plan = nullptr;
-    s = choose_plan(ctx, replicas, o, &plan);
-    if (s != HQA_OK) return s;
+    if (!dense) {
+        s = choose_plan(ctx, replicas, o, &plan);
+        if (s != HQA_OK) return s;
+    }
     s = upload_schedule(ctx, sched, dt, steps);
     if (s != HQA_OK) return s;
 
@@ -405,7 +421,11 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     int8_t* spins = out->spins;
     if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
 
-    if (plan->vec)
+    if (dense)
+        s = hqa_dense_launch_md(ctx, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
+                                o.phi0, o.p0, sched->M, out->phi, out->p, phibar,
+                                o.precision == HQA_PREC_BF16X2, st);
+    else if (plan->vec)
         s = hqa_vec_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
                               o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
     else
@@ -434,11 +454,16 @@ hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, flo
     else hqa_run_opts_default(&o);
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (o.kernel == HQA_KERNEL_DENSE || (o.kernel == HQA_KERNEL_AUTO && ctx->dense_tc &&
+                                         o.precision == HQA_PREC_BF16)) {
+        if (!ctx->dense_tc || o.precision != HQA_PREC_BF16) return HQA_ERR_UNSUPPORTED;
+        return hqa_dense_field(ctx, replicas, phi, L, st);
+    }
+    if (!ctx->unit || o.precision == HQA_PREC_BF16X2) return HQA_ERR_UNSUPPORTED;
     const SparsePlan* plan = nullptr;
     s = choose_plan(ctx, replicas, o, &plan);
     if (s != HQA_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (plan->vec) return hqa_vec_launch_field(ctx, plan, replicas, phi, L, st);
     return hqa_sparse_launch_field(ctx, plan, replicas, phi, L, st);
 }
@@ -479,7 +504,23 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
     else hqa_run_opts_default(&o);
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    if (!ctx->unit) return HQA_ERR_UNSUPPORTED;
+    const bool tc_prec = o.precision == HQA_PREC_BF16 || o.precision == HQA_PREC_BF16X2;
+    if (o.kernel == HQA_KERNEL_DENSE ||
+        (o.kernel == HQA_KERNEL_AUTO && tc_prec && hqa_dense_md_possible(ctx, replicas))) {
+        int nh = 0, grid = 0;
+        if (!ctx->dense_tc || !tc_prec || !hqa_dense_md_geometry(ctx, replicas, &nh, &grid))
+            return HQA_ERR_UNSUPPORTED;
+        out->kernel = HQA_KERNEL_DENSE;
+        out->replicas_per_block = 2 * nh;
+        out->blocks = grid;
+        out->threads = 320;
+        out->smem_bytes = 0;
+        out->pad_ratio = (double)grid * 128 * 2 * nh / ((double)ctx->N * replicas);
+        out->conflict_ratio = 1.0;
+        out->balance = 1.0;
+        return HQA_OK;
+    }
+    if (!ctx->unit || o.precision == HQA_PREC_BF16X2) return HQA_ERR_UNSUPPORTED;
     const SparsePlan* plan = nullptr;
     s = choose_plan(ctx, replicas, o, &plan);
     if (s != HQA_OK) return s;

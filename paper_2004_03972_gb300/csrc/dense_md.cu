@@ -1,0 +1,695 @@
+// dense_md.cu -- dense local field on the tcgen05 tensor cores.
+//
+// For dense couplings the field of all replicas is one GEMM per step,
+//   L[i][r] = sum_j J[i][j] Phi[j][r]   (Methods, "Leapfrog algorithm"),
+// with J (N x N, exactly representable in BF16, e.g. +-1) as the A operand
+// and the BF16 copy of phi, replica-major ([R][K], K contiguous), as the B
+// operand; both are K-major.  A CTA owns a 128-row x BN-replica output tile:
+//   warp 0      TMA producer (one elected thread): 128 x 64 tile of J and
+//               BN x 64 tile of Phi per stage, 128-byte swizzle, mbarrier
+//               completion with transaction bytes;
+//   warp 1      TMEM allocation and the MMA issuer (one elected thread):
+//               4 x tcgen05.mma (M=128, N=BN, K=16) per stage into an FP32
+//               accumulator in tensor memory, tcgen05.commit frees the stage;
+//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 16 columns, warp w reading
+//               TMEM lanes 32*(w%4) .. +31 (rows), coalesced FP32 stores.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "hqa_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                  // one 128-byte swizzle row of BF16
+constexpr int kFieldBN = 128;
+constexpr int kFieldStages = 4;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+__global__ void k_phi_to_bf16(const float* __restrict__ phi, int R, int N, int Rpad, int Kpad,
+                              __nv_bfloat16* __restrict__ out)
+{
+    const size_t total = (size_t)Rpad * Kpad;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / Kpad), k = (int)(idx % Kpad);
+        const float v = (r < R && k < N) ? phi[(size_t)r * N + k] : 0.f;
+        out[idx] = __float2bfloat16_rn(v);
+    }
+}
+
+struct FieldArgs {
+    float* L;            // [R][N]
+    const float* phi;    // [R][N], for the 2 h |phi| term
+    const float* h;      // [N] or null
+    uint32_t* status;
+    int N, R, KT;        // KT = Kpad / BK
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+k_dense_field(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
+              const FieldArgs a)
+{
+    constexpr uint32_t A_BYTES = BM * BK * 2;
+    constexpr uint32_t B_BYTES = BN * BK * 2;
+    constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned operand region
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t bar = base + STAGES * STAGE_BYTES;   // full[S], empty[S], accf
+    const uint32_t full0 = bar, empty0 = bar + 8 * STAGES, accf = bar + 16 * STAGES;
+    const uint32_t tmem_slot = accf + 8;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(full0 + 8 * s, 1);
+            tc::mbar_init(empty0 + 8 * s, 1);
+        }
+        tc::mbar_init(accf, 1);
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&tmJ);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tmem_slot));
+    volatile int* abort = &s_abort;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        for (int kt = 0; kt < a.KT; ++kt) {
+            const int s = kt % STAGES;
+            if (kt >= STAGES && !tc::mbar_wait(empty0 + 8 * s, ((kt / STAGES) - 1) & 1, abort, kWaitNs))
+                break;
+            const uint32_t sa = base + s * STAGE_BYTES;
+            tc::mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+            tc::tma_load_2d(sa, &tmJ, kt * BK, m0, full0 + 8 * s);
+            tc::tma_load_2d(sa + A_BYTES, &tmB, kt * BK, n0, full0 + 8 * s);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        constexpr uint32_t idesc = tc::idesc_bf16(BM, BN);
+        for (int kt = 0; kt < a.KT; ++kt) {
+            const int s = kt % STAGES;
+            if (!tc::mbar_wait(full0 + 8 * s, (kt / STAGES) & 1, abort, kWaitNs)) break;
+            tc::tc_fence_after();
+            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint64_t ad = tc::sdesc_k128(sa), bd = tc::sdesc_k128(sa + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)  // 16 BF16 = 32 bytes per MMA along K
+                tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+            tc::mma_commit(empty0 + 8 * s);
+        }
+        tc::mma_commit(accf);
+    } else if (warp >= 2) {
+        // ---- epilogue: TMEM -> registers -> global ----
+        const int quarter = warp & 3;
+        // warp-uniform outcome: tcgen05.ld is a whole-warp instruction
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(accf, 0, abort, kWaitNs));
+        tc::tc_fence_after();
+        if (ok) {
+            const int row = m0 + 32 * quarter + lane;
+            const float hr = (a.h && row < a.N) ? 2.f * a.h[row] : 0.f;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+                tc::tmem_wait_ld();
+                if (row < a.N) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int r = n0 + c0 + c;
+                        if (r < a.R) {
+                            float L = __uint_as_float(v[c]);
+                            if (hr != 0.f) L += hr * fabsf(a.phi[(size_t)r * a.N + row]);
+                            a.L[(size_t)r * a.N + row] = L;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (*abort && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_TIMEOUT);
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor [rows][cols] (cols contiguous, cols * 2 bytes a multiple of
+// 16), box {64 cols, box_rows}, 128-byte swizzle.
+bool make_tmap_bf16(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+size_t field_smem()
+{
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 16 * STAGES + 64;
+}
+
+}  // namespace
+
+// Builds the BF16 copy of J ([Mpad][Mpad], zero padded) and its tensor map.
+hqa_status hqa_dense_setup(hqa_ctx* ctx, const float* J)
+{
+    const int N = ctx->N;
+    const int Mpad = (N + BM - 1) / BM * BM;
+    std::vector<__nv_bfloat16> jb((size_t)Mpad * Mpad, __float2bfloat16_rn(0.f));
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            const float v = (i == j) ? 0.f : J[(size_t)i * N + j];
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            if (__bfloat162float(b) != v) return HQA_OK;  // not exact in BF16: no tensor-core path
+            jb[(size_t)i * Mpad + j] = b;
+        }
+    if (!get_encode()) return HQA_OK;
+    void* d = nullptr;
+    HQA_CUDA_TRY(cudaMalloc(&d, jb.size() * sizeof(__nv_bfloat16)));
+    HQA_CUDA_TRY(cudaMemcpy(d, jb.data(), jb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+    ctx->d_Jbf = d;
+    ctx->Mpad = Mpad;
+    if (!make_tmap_bf16(&ctx->tmJ, d, Mpad, Mpad, BM)) return HQA_ERR_CUDA;
+    ctx->dense_tc = true;
+    return HQA_OK;
+}
+
+hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, cudaStream_t st)
+{
+    if (!ctx->dense_tc) return HQA_ERR_UNSUPPORTED;
+    const int Kpad = ctx->Mpad;
+    const int Rpad = (R + kFieldBN - 1) / kFieldBN * kFieldBN;
+    const size_t bytes = (size_t)Rpad * Kpad * sizeof(__nv_bfloat16);
+    hqa_status s = hqa_reserve(&ctx->d_ws, &ctx->ws_cap, bytes);
+    if (s != HQA_OK) return s;
+    __nv_bfloat16* phib = static_cast<__nv_bfloat16*>(ctx->d_ws);
+    k_phi_to_bf16<<<std::min<size_t>(4096, (bytes / 2 + 255) / 256), 256, 0, st>>>(phi, R, ctx->N, Rpad,
+                                                                                   Kpad, phib);
+    CUtensorMap tmB;
+    if (!make_tmap_bf16(&tmB, phib, Rpad, Kpad, kFieldBN)) return HQA_ERR_CUDA;
+    FieldArgs a{};
+    a.L = L;
+    a.phi = phi;
+    a.h = ctx->has_h ? ctx->d_h : nullptr;
+    a.status = ctx->d_status;
+    a.N = ctx->N;
+    a.R = R;
+    a.KT = Kpad / BK;
+    const size_t smem = field_smem<kFieldBN, kFieldStages>();
+    cudaError_t e = cudaFuncSetAttribute(k_dense_field<kFieldBN, kFieldStages>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return HQA_ERR_CUDA;
+    const dim3 grid(ctx->Mpad / BM, Rpad / kFieldBN);
+    k_dense_field<kFieldBN, kFieldStages><<<grid, 192, smem, st>>>(ctx->tmJ, tmB, a);
+    return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
+
+// ===========================================================================
+// Persistent dense MD kernel.
+//
+// Grid: Mt x Nc CTAs, all co-resident (cooperative launch), 1 per SM.  CTA
+// (mt, nc) owns spin rows [128 mt, +128) and replica columns [2 NH nc, +2 NH),
+// split into two halves h = 0, 1 of NH columns with their own TMEM
+// accumulator.  Per leapfrog step m and half h:
+//   producer  waits until all Mt CTAs of column group (nc, h) finished the
+//             epilogue of (m-1, h) (arrival counter >= Mt m), then streams the
+//             J and Phi^(m) k-tiles through the shared-memory ring;
+//   MMA       waits for accumulator h to be drained, accumulates L = J Phi;
+//   epilogue  8 warps read L from TMEM and do the kick and drift of Methods'
+//             leapfrog on the FP32 state in global memory ([R][Npad], one
+//             owner per element), write the BF16 Phi^(m+1) into the other
+//             buffer and the window sum, release accumulator h and arrive on
+//             the counter.
+// While the epilogue drains half h, the MMA of the other half runs.
+// ===========================================================================
+namespace {
+
+constexpr int kEpiWarps = 8;
+constexpr int kMDThreads = 64 + 32 * kEpiWarps;
+
+struct DenseMDArgs {
+    float* phi;              // [Rpad][Npad] FP32 master
+    float* p;                // [Rpad][Npad]
+    float* w;                // [Rpad][Npad] window sums
+    __nv_bfloat16* phib;     // [2][Rpad][Npad] operand buffers
+    const StepCoef* sched;
+    const float* h;          // [N] or null
+    unsigned int* gbar;      // [2 Nc] arrival counters
+    uint32_t* status;
+    int64_t S;
+    int W, N, Npad, Rpad, R, KT, Mt, M;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int NH, int STAGES, bool SPLIT>
+__global__ void __launch_bounds__(kMDThreads, 1)
+k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
+           const DenseMDArgs a)
+{
+    constexpr uint32_t A_BYTES = BM * BK * 2;
+    constexpr uint32_t B_BYTES = NH * BK * 2;
+    constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr uint32_t TMEM_COLS = 2 * NH <= 64 ? 64 : 2 * NH <= 128 ? 128 : 2 * NH <= 256 ? 256 : 512;
+    static_assert(NH % 16 == 0 && NH <= 256, "UMMA N");
+    static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t bar = base + STAGES * STAGE_BYTES;
+    const uint32_t full0 = bar, empty0 = bar + 8 * STAGES;
+    const uint32_t accf0 = bar + 16 * STAGES, acce0 = accf0 + 16;
+    const uint32_t tmem_slot = acce0 + 16;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x % a.Mt, nc = blockIdx.x / a.Mt;
+    const int m0 = mt * BM, n0 = nc * 2 * NH;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(full0 + 8 * s, 1);
+            tc::mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int hh = 0; hh < 2; ++hh) {
+            tc::mbar_init(accf0 + 8 * hh, 1);
+            tc::mbar_init(acce0 + 8 * hh, kEpiWarps);
+        }
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&tmJ);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    uint32_t tmem;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tmem_slot));
+    volatile int* abort = &s_abort;
+    volatile uint32_t* gstatus = a.status;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            uint32_t it = 0;
+            for (int64_t m = 0; m < a.S && !*abort; ++m) {
+                for (int hh = 0; hh < 2 && !*abort; ++hh) {
+                    if (m > 0) {
+                        const unsigned int* g = a.gbar + 2 * nc + hh;
+                        const unsigned int target = (unsigned int)(a.Mt * m);
+                        const uint64_t t0 = tc::globaltimer();
+                        uint32_t spins = 0;
+                        while (ld_acquire(g) < target) {
+                            if ((++spins & 63u) == 0) {
+                                if (*abort || (*gstatus & HQA_DEV_TIMEOUT)) { *abort = 1; break; }
+                                if (tc::globaltimer() - t0 > kWaitNs) { *abort = 1; break; }
+                            }
+                        }
+                        if (*abort) break;
+                        tc::fence_proxy_async_global();
+                    }
+                    const int brow = (int)(m & 1) * a.Rpad + n0 + hh * NH;
+                    // split operand: K runs over [hi | lo], J is reused for both halves
+                    const int KTT = SPLIT ? 2 * a.KT : a.KT;
+                    for (int kt = 0; kt < KTT; ++kt, ++it) {
+                        const int s = it % STAGES;
+                        if (it >= STAGES &&
+                            !tc::mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort, kWaitNs))
+                            break;
+                        const uint32_t sa = base + s * STAGE_BYTES;
+                        tc::mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+                        tc::tma_load_2d(sa, &tmJ, (kt % a.KT) * BK, m0, full0 + 8 * s);
+                        tc::tma_load_2d(sa + A_BYTES, &tmB, kt * BK, brow, full0 + 8 * s);
+                    }
+                }
+            }
+            // drain: every issued stage must land before the CTA can exit
+            if (*abort)
+                for (uint32_t k = (it > STAGES ? it - STAGES : 0); k < it; ++k)
+                    tc::mbar_wait(full0 + 8 * (k % STAGES), (k / STAGES) & 1, abort, 100000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            constexpr uint32_t idesc = tc::idesc_bf16(BM, NH);
+            uint32_t it = 0;
+            for (int64_t m = 0; m < a.S && !*abort; ++m) {
+                for (int hh = 0; hh < 2 && !*abort; ++hh) {
+                    if (m > 0 && !tc::mbar_wait(acce0 + 8 * hh, (uint32_t)((m - 1) & 1), abort, kWaitNs))
+                        break;
+                    tc::tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(hh * NH);
+                    const int KTT = SPLIT ? 2 * a.KT : a.KT;
+                    for (int kt = 0; kt < KTT; ++kt, ++it) {
+                        const int s = it % STAGES;
+                        if (!tc::mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort, kWaitNs)) break;
+                        tc::tc_fence_after();
+                        const uint32_t sa = base + s * STAGE_BYTES;
+                        const uint64_t ad = tc::sdesc_k128(sa), bd = tc::sdesc_k128(sa + A_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+                        tc::mma_commit(empty0 + 8 * s);
+                    }
+                    tc::mma_commit(accf0 + 8 * hh);
+                }
+            }
+        }
+    } else {
+        // ---- epilogue warps: kick, drift, BF16 shadow, window ----
+        const int ew = warp - 2;              // 0..7
+        const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
+        const int csel = ew >> 2;             // chunk parity handled by this warp
+        const int row = m0 + 32 * quarter + lane;
+        const bool row_ok = row < a.N;
+        const float hr = (a.h && row_ok) ? 2.f * a.h[row] : 0.f;
+        const int mhalf = (a.M - 2) / 2;
+        const int64_t win0 = a.S - (int64_t)a.W;
+        bool stop = false;
+        for (int64_t m = 0; m < a.S && !stop; ++m) {
+            const float4 cf = __ldg(reinterpret_cast<const float4*>(a.sched) + m);
+            const bool in_win = m >= win0;
+            const int Kb = SPLIT ? 2 * a.Npad : a.Npad;   // operand row: [hi | lo] when split
+            __nv_bfloat16* nb = a.phib + (size_t)((m + 1) & 1) * a.Rpad * Kb;
+            for (int hh = 0; hh < 2 && !stop; ++hh) {
+                const bool ok = __all_sync(0xffffffffu,
+                                           tc::mbar_wait(accf0 + 8 * hh, (uint32_t)(m & 1), abort, kWaitNs));
+                tc::tc_fence_after();
+                if (ok) {
+#pragma unroll 1
+                    for (int c = csel; c < NH / 16; c += 2) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(hh * NH + c * 16), v);
+                        tc::tmem_wait_ld();
+                        if (row_ok) {
+                            const int rbase = n0 + hh * NH + c * 16;
+                            float ph[16], pp[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const size_t o = (size_t)(rbase + j) * a.Npad + row;
+                                ph[j] = a.phi[o];
+                                pp[j] = a.p[o];
+                            }
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const size_t o = (size_t)(rbase + j) * a.Npad + row;
+                                const float L = __uint_as_float(v[j]) + hr * fabsf(ph[j]);
+                                const float phi2 = ph[j] * ph[j];
+                                float pw = ph[j];
+                                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                                const float pn = pp[j] - fmaf(cf.x, pw, cf.y * L);
+                                const float fn = fmaf(cf.z, pn, ph[j]);
+                                a.p[o] = pn;
+                                a.phi[o] = fn;
+                                const size_t ob = (size_t)(rbase + j) * Kb + row;
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(fn);
+                                nb[ob] = hi;
+                                if (SPLIT) nb[ob + a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                if (in_win) a.w[o] += fn;
+                            }
+                        }
+                    }
+                    // accumulator h may be overwritten once every epilogue warp has read it
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(acce0 + 8 * hh);
+                }
+                // Phi^(m+1) of this half -> visible to the other CTAs' TMA loads
+                tc::fence_proxy_async_global();
+                // all epilogue warps meet here every half-step; the barrier also
+                // ORs the abort flags so every warp leaves at the same point
+                uint32_t any;
+                asm volatile(
+                    "{\n\t.reg .pred q, r;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                    "barrier.red.or.pred r, 1, %2, q;\n\tselp.u32 %0, 1, 0, r;\n\t}"
+                    : "=r"(any) : "r"((uint32_t)(!ok || *abort)), "n"(32 * kEpiWarps) : "memory");
+                if (any) {
+                    *abort = 1;
+                    stop = true;
+                } else if (ew == 0 && lane == 0) {
+                    __threadfence();
+                    atomicAdd(a.gbar + 2 * nc + hh, 1u);
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (*abort && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_TIMEOUT);
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// State set-up: phi(0), p(0) (SplitMix64 or caller-given), window 0, BF16
+// operand buffer 0; padding rows/replicas zero in every array.
+__global__ void k_dense_init(DenseMDArgs a, uint64_t seed, int init, const float* phi0,
+                             const float* p0, int split)
+{
+    const int Kb = split ? 2 * a.Npad : a.Npad;
+    const size_t total = (size_t)a.Rpad * a.Npad;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / a.Npad), i = (int)(idx % a.Npad);
+        float phi = 0.f, p = 0.f;
+        if (r < a.R && i < a.N) {
+            const uint64_t c = ((uint64_t)r << 32) | (uint64_t)i;
+            if (init == HQA_INIT_GIVEN) {
+                phi = phi0[(size_t)r * a.N + i];
+                p = p0[(size_t)r * a.N + i];
+            } else {
+                uint64_t z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;  // SplitMix64
+                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                z ^= z >> 31;
+                p = (z >> 63) ? -1.f : 1.f;
+                if (init == HQA_INIT_RANDOM_FLUX) {
+                    uint64_t y = seed + ((c | (1ull << 62)) + 1ull) * 0x9E3779B97F4A7C15ull;
+                    y = (y ^ (y >> 30)) * 0xBF58476D1CE4E5B9ull;
+                    y = (y ^ (y >> 27)) * 0x94D049BB133111EBull;
+                    y ^= y >> 31;
+                    phi = (float)((int64_t)(y >> 40) - (1 << 23)) * 0x1p-26f;
+                }
+            }
+        }
+        a.phi[idx] = phi;
+        a.p[idx] = p;
+        a.w[idx] = 0.f;
+        const size_t ob = (size_t)r * Kb + i;
+        const size_t buf = (size_t)a.Rpad * Kb;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(phi);
+        a.phib[ob] = hi;
+        a.phib[buf + ob] = __float2bfloat16_rn(0.f);
+        if (split) {
+            a.phib[ob + a.Npad] = __float2bfloat16_rn(phi - __bfloat162float(hi));
+            a.phib[buf + ob + a.Npad] = __float2bfloat16_rn(0.f);
+        }
+    }
+}
+
+__global__ void k_dense_out(DenseMDArgs a, float inv_w, float* phi_out, float* p_out,
+                            float* phibar_out)
+{
+    const size_t total = (size_t)a.R * a.N;
+    bool bad = false;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / a.N), i = (int)(idx % a.N);
+        const size_t o = (size_t)r * a.Npad + i;
+        const float phi = a.phi[o], p = a.p[o];
+        if (phi_out) phi_out[idx] = phi;
+        if (p_out) p_out[idx] = p;
+        if (phibar_out) phibar_out[idx] = a.w[o] * inv_w;
+        bad |= !(isfinite(phi) && isfinite(p));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_NONFINITE);
+}
+
+template <int NH, int STAGES>
+size_t md_smem()
+{
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + NH * BK * 2) + 16 * STAGES + 64 + 64;
+}
+
+// Column halves: NH replicas (multiple of 16, <= 256); Nc = ceil(R / 2NH) with
+// Mt * Nc <= SMs.  Only instantiated widths are offered.
+constexpr int kNHs[] = {256, 240, 224, 192, 160, 128, 96, 64, 32, 16};
+
+int pick_nh(int Mt, int R, int sms)
+{
+    const int nc_max = sms / Mt;
+    if (nc_max < 1) return 0;
+    int best = 0;
+    double best_t = 1e30;
+    for (int nh : kNHs) {
+        const int nc = (R + 2 * nh - 1) / (2 * nh);
+        if (nc > nc_max) continue;
+        // time ~ columns per CTA (all CTAs run concurrently); prefer fewer padded columns
+        const double t = (double)nh + 1e-3 * (double)(nc * 2 * nh - R);
+        if (t < best_t) { best_t = t; best = nh; }
+    }
+    return best;
+}
+
+}  // namespace
+
+template <int NH, bool SPLIT>
+static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
+                                    const CUtensorMap& tmB)
+{
+    constexpr int STAGES = 4;
+    const size_t smem = md_smem<NH, STAGES>();
+    if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
+    if (cudaFuncSetAttribute(k_dense_md<NH, STAGES, SPLIT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return HQA_ERR_CUDA;
+    void* args[] = {const_cast<CUtensorMap*>(&ctx->tmJ), const_cast<CUtensorMap*>(&tmB),
+                    const_cast<DenseMDArgs*>(&a)};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_dense_md<NH, STAGES, SPLIT>,
+                                                dim3(grid), dim3(kMDThreads), args, smem, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        (void)cudaGetLastError();
+        return HQA_ERR_TOO_LARGE;
+    }
+    return e == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
+
+bool hqa_dense_md_possible(const hqa_ctx* ctx, int32_t R)
+{
+    if (!ctx->dense_tc) return false;
+    return pick_nh(ctx->Mpad / BM, R, ctx->sm_count) > 0;
+}
+
+int hqa_dense_md_geometry(const hqa_ctx* ctx, int32_t R, int* nh, int* grid)
+{
+    const int Mt = ctx->Mpad / BM;
+    const int h = pick_nh(Mt, R, ctx->sm_count);
+    if (h == 0) return 0;
+    const int nc = (R + 2 * h - 1) / (2 * h);
+    *nh = h;
+    *grid = Mt * nc;
+    return 1;
+}
+
+hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
+                               int32_t R, uint64_t seed, int init, const float* phi0,
+                               const float* p0, int M, float* phi_out, float* p_out,
+                               float* phibar_out, bool split, cudaStream_t st)
+{
+    int NH = 0, grid = 0;
+    if (!hqa_dense_md_geometry(ctx, R, &NH, &grid)) return HQA_ERR_TOO_LARGE;
+    const int Mt = ctx->Mpad / BM;
+    const int Nc = grid / Mt;
+    const int Rpad = Nc * 2 * NH;
+    const int Npad = ctx->Mpad;
+    const size_t n = (size_t)Rpad * Npad;
+    const size_t nb = split ? 2 * n : n;   // operand elements per buffer
+    // state: phi, p, w (FP32), two BF16 operand buffers, 2 Nc counters
+    const size_t off_p = n * 4, off_w = 2 * n * 4, off_b = 3 * n * 4, off_g = off_b + 2 * nb * 2;
+    const size_t need = off_g + (size_t)2 * Nc * sizeof(unsigned int);
+    hqa_status s = hqa_reserve(&ctx->d_state, &ctx->state_cap, need);
+    if (s != HQA_OK) return s;
+    char* b = static_cast<char*>(ctx->d_state);
+    DenseMDArgs a{};
+    a.phi = reinterpret_cast<float*>(b);
+    a.p = reinterpret_cast<float*>(b + off_p);
+    a.w = reinterpret_cast<float*>(b + off_w);
+    a.phib = reinterpret_cast<__nv_bfloat16*>(b + off_b);
+    a.gbar = reinterpret_cast<unsigned int*>(b + off_g);
+    a.sched = d_sched;
+    a.h = ctx->has_h ? ctx->d_h : nullptr;
+    a.status = ctx->d_status;
+    a.S = S;
+    a.W = W;
+    a.N = ctx->N;
+    a.Npad = Npad;
+    a.Rpad = Rpad;
+    a.R = R;
+    a.KT = Npad / BK;
+    a.Mt = Mt;
+    a.M = M;
+    CUtensorMap tmB;
+    if (!make_tmap_bf16(&tmB, a.phib, (uint64_t)2 * Rpad, split ? 2 * Npad : Npad, NH))
+        return HQA_ERR_CUDA;
+    k_dense_init<<<std::min<size_t>(8192, (n + 255) / 256), 256, 0, st>>>(a, seed, init, phi0, p0,
+                                                                         split ? 1 : 0);
+    if (cudaMemsetAsync(a.gbar, 0, (size_t)2 * Nc * sizeof(unsigned int), st) != cudaSuccess)
+        return HQA_ERR_CUDA;
+#define HQA_NH_CASE(V)                                                                        \
+    case V:                                                                                    \
+        s = split ? launch_dense_md_t<V, true>(ctx, a, grid, st, tmB)                          \
+                  : launch_dense_md_t<V, false>(ctx, a, grid, st, tmB);                        \
+        break;
+    switch (NH) {
+        HQA_NH_CASE(256)
+        HQA_NH_CASE(240)
+        HQA_NH_CASE(224)
+        HQA_NH_CASE(192)
+        HQA_NH_CASE(160)
+        HQA_NH_CASE(128)
+        HQA_NH_CASE(96)
+        HQA_NH_CASE(64)
+        HQA_NH_CASE(32)
+        HQA_NH_CASE(16)
+    default: return HQA_ERR_TOO_LARGE;
+    }
+#undef HQA_NH_CASE
+    if (s != HQA_OK) return s;
+    const int64_t nwin = S < W ? S : W;
+    k_dense_out<<<std::min<size_t>(8192, ((size_t)R * ctx->N + 255) / 256), 256, 0, st>>>(
+        a, 1.0f / (float)nwin, phi_out, p_out, phibar_out);
+    return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}

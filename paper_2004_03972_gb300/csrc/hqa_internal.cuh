@@ -2,6 +2,7 @@
 // the library's translation units (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -108,6 +109,12 @@ struct hqa_ctx {
     void* d_sub = nullptr;
     size_t sub_cap = 0;
     uint32_t* d_status = nullptr;
+
+    // dense contexts whose couplings are exact in BF16: tensor-core operand
+    bool dense_tc = false;
+    void* d_Jbf = nullptr;         // [Mpad][Mpad] BF16, zero padded
+    int Mpad = 0;
+    CUtensorMap tmJ;               // TMA map of d_Jbf, 128 x 64 boxes
 };
 
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;
@@ -135,6 +142,16 @@ hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const Step
                                 float* p_out, float* phibar_out, cudaStream_t st);
 hqa_status hqa_sparse_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t R,
                                    const float* phi, float* L, cudaStream_t st);
+
+// dense_md.cu
+hqa_status hqa_dense_setup(hqa_ctx* ctx, const float* J);
+hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, cudaStream_t st);
+bool hqa_dense_md_possible(const hqa_ctx* ctx, int32_t R);
+int hqa_dense_md_geometry(const hqa_ctx* ctx, int32_t R, int* nh, int* grid);
+hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
+                               int32_t R, uint64_t seed, int init, const float* phi0,
+                               const float* p0, int M, float* phi_out, float* p_out,
+                               float* phibar_out, bool split, cudaStream_t st);
 
 // readout.cu
 hqa_status hqa_launch_readout(hqa_ctx* ctx, int32_t R, const float* phibar, int32_t n,

@@ -1,0 +1,149 @@
+"""GPU parity of the dense tensor-core (tcgen05) path against the FP64 oracle.
+
+BF16 operand with FP32 accumulation: per element
+  e_i = |L_gpu - L_ref| / (|L_ref| + sum_j |J_ij| |phi_j| + 2 |h_i| |phi_i|) <= 1e-2,
+and in practice <= 2^-8 (the BF16 rounding of phi).
+"""
+import numpy as np
+import pytest
+
+from paper_2004_03972_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hqa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_03972_gb300 import build, hqa as H
+    build.build()
+    return H
+
+
+def _field_err(inst, phi, L):
+    J = inst.to_dense()
+    ref = phi.astype(np.float64) @ J.T
+    scale = np.abs(phi.astype(np.float64)) @ np.abs(J).T
+    if inst.h is not None:
+        ref += 2 * inst.h * np.abs(phi)
+        scale += 2 * np.abs(inst.h) * np.abs(phi)
+    return np.max(np.abs(L - ref) / (np.abs(ref) + scale + 1e-30))
+
+
+@pytest.mark.parametrize("N,R", [(100, 1), (100, 130), (300, 77), (1000, 256), (2000, 300)])
+def test_dense_field_matches_oracle(hqa, orc, N, R):
+    inst = instances.sk_pm1(N, 50 + N)
+    ctx = hqa.Context.from_instance(inst)
+    rng = np.random.default_rng(N + R)
+    phi = rng.uniform(-1.3, 1.3, size=(R, N)).astype(np.float32)
+    L = ctx.local_field(torch.from_numpy(phi).cuda(), precision=hqa.PREC_BF16,
+                        kernel=hqa.KERNEL_DENSE)
+    ctx.sync()
+    L = L.cpu().numpy().astype(np.float64)
+    # oracle (a few replicas) and the matrix form agree; check both
+    pr = orc.Problem.from_instance(inst)
+    for r in (0, R - 1):
+        ref = orc.beta_field(pr, phi[r].astype(np.float64))
+        scale = np.abs(phi[r].astype(np.float64)) @ np.abs(inst.dense).T
+        assert np.max(np.abs(L[r] - ref) / (np.abs(ref) + scale)) <= 1e-2
+    assert _field_err(inst, phi, L) <= 2.0 ** -8
+
+
+def test_dense_field_with_field_term(hqa):
+    inst = instances.with_integer_field(instances.sk_pm1(260, 3), 2, 7)
+    ctx = hqa.Context.from_instance(inst)
+    rng = np.random.default_rng(1)
+    phi = rng.uniform(-1, 1, size=(40, inst.N)).astype(np.float32)
+    L = ctx.local_field(torch.from_numpy(phi).cuda(), precision=hqa.PREC_BF16,
+                        kernel=hqa.KERNEL_DENSE)
+    ctx.sync()
+    assert _field_err(inst, phi, L.cpu().numpy().astype(np.float64)) <= 2.0 ** -8
+
+
+def test_dense_path_requires_bf16_exact_couplings(hqa):
+    inst = instances.uniform_sg(64, 2)   # real-valued J: not exact in BF16
+    J = inst.dense.astype(np.float32)
+    J = (J + J.T) / 2
+    ctx = hqa.Context.from_dense(J)
+    phi = torch.zeros((2, 64), device="cuda")
+    with pytest.raises(hqa.HQAError) as ei:
+        ctx.local_field(phi, precision=hqa.PREC_BF16, kernel=hqa.KERNEL_DENSE)
+    assert ei.value.status == 6
+
+
+def _close(gpu, ref, tol, scale=None):
+    s = np.max(np.abs(ref)) if scale is None else max(scale, np.max(np.abs(ref)))
+    return np.max(np.abs(gpu - ref)) <= tol * s
+
+
+# States after <= 100 steps vs the FP64 oracle (phi on its own scale, p on the momentum
+# scale |p(0)| = 1).  Split operand (hi + lo BF16): within 1e-2 at every size.  Plain BF16
+# operand: the rounding of phi alone moves the dense-SK state by 0.28 %, 1.2 % and 4.0 %
+# after 100 steps at N = 100, 300, 2000 (CPU emulation of that rounding with everything
+# else in FP64); the stated bounds are twice that.
+@pytest.mark.parametrize("N,R,S,prec,tol", [
+    (100, 8, 60, 2, 1e-2), (300, 64, 100, 2, 1e-2), (300, 700, 40, 2, 1e-2),
+    (2000, 300, 100, 2, 1e-2),
+    (100, 8, 60, 1, 1e-2), (300, 64, 100, 1, 2.5e-2), (2000, 300, 100, 1, 1e-1)])
+def test_dense_md_states_match_oracle(hqa, orc, N, R, S, prec, tol):
+    inst = instances.sk_pm1(N, 7 + N)
+    ctx = hqa.Context.from_instance(inst)
+    dt = 1.0 / 10000
+    out = ctx.run(S, R, seed=21, dt=dt, precision=prec, kernel=hqa.KERNEL_DENSE,
+                  outputs=("phi", "p", "phibar"))
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    for r in sorted({0, R // 2, R - 1}):
+        ophi, op, opbar = orc.md_run(pr, S, dt=dt, p0=orc.initial_momenta(21, r, N))
+        assert _close(out["phi"][r].cpu().numpy(), ophi, tol)
+        assert _close(out["p"][r].cpu().numpy(), op, tol, scale=1.0)
+        assert _close(out["phibar"][r].cpu().numpy(), opbar, tol, scale=np.max(np.abs(ophi)))
+
+
+def test_dense_md_matches_vector_kernel_statistically(hqa):
+    """Dense tensor-core and sparse vector kernels run the same BF16-operand recurrence;
+    after 100 steps they agree to the BF16 tolerance."""
+    inst = instances.sk_pm1(256, 3)
+    ctx = hqa.Context.from_instance(inst)
+    a = ctx.run(100, 64, seed=4, dt=1e-4, precision=hqa.PREC_BF16, kernel=hqa.KERNEL_DENSE,
+                outputs=("phi",))
+    b = ctx.run(100, 64, seed=4, dt=1e-4, precision=hqa.PREC_BF16, kernel=hqa.KERNEL_VECTOR,
+                outputs=("phi",), replicas_per_block=8)
+    ctx.sync()
+    d = (a["phi"] - b["phi"]).abs().max().item()
+    assert d <= 1e-2 * b["phi"].abs().max().item()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_dense_md_z2_bitwise(hqa, prec):
+    inst = instances.sk_pm1(384, 9)
+    ctx = hqa.Context.from_instance(inst)
+    R = 96
+    g = torch.Generator().manual_seed(3)
+    p0 = (torch.randint(0, 2, (R, inst.N), generator=g) * 2 - 1).float().cuda()
+    z = torch.zeros(R, inst.N, device="cuda")
+    kw = dict(init=hqa.INIT_GIVEN, phi0=z, precision=prec, kernel=hqa.KERNEL_DENSE,
+              outputs=("phi", "p", "phibar"))
+    a = ctx.run(300, R, p0=p0, **kw)
+    b = ctx.run(300, R, p0=-p0, **kw)
+    ctx.sync()
+    for k in ("phi", "p", "phibar"):
+        assert torch.equal(a[k], -b[k])
+
+
+def test_dense_md_pipeline_readout_energy(hqa, orc):
+    inst = instances.sk_pm1(500, 12)
+    ctx = hqa.Context.from_instance(inst)
+    R, n = 40, 16
+    out = ctx.run(400, R, seed=2, precision=hqa.PREC_BF16, sched=hqa.schedule(n_ambivalent=n))
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    pbar = out["phibar"].cpu().numpy().astype(np.float64)
+    for r in (0, 17, R - 1):
+        s, f = orc.readout(pbar[r], n)
+        assert np.array_equal(out["spins"][r].cpu().numpy(), s)
+        assert np.array_equal(out["frozen"][r].cpu().numpy(), f)
+        assert int(out["energy"][r]) == orc.energy_int(pr, s)
+        assert int(out["cut"][r]) == orc.cut_int(pr, s)
