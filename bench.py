@@ -203,7 +203,9 @@ def run_ours(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     build.build()
-    cfg = CONFIGS[args.config]
+    cfg = dict(CONFIGS[args.config])
+    if args.md_steps:
+        cfg["S"] = args.md_steps
     inst = make_instance(args.config)
     N, R, S, n = inst.N, cfg["R"], cfg["S"], cfg["n"]
     ctx = hqa.Context.from_instance(inst)
@@ -351,7 +353,9 @@ def run_ours(args):
         "dtype": {"PREC_FP32": "f32", "PREC_BF16": "bf16-operand/f32-accumulate",
                   "PREC_BF16X2": "bf16x2-split-operand/f32-accumulate"}[hv["prec_name"]],
         "data": "synthetic (seeded instance generator)",
-        "config": {"workload": cfg["desc"], "N": N, "nnz": inst.nnz, "replicas": R, "md_steps": S,
+        "config": {"workload": cfg["desc"] if S == CONFIGS[args.config]["S"] else
+                   cfg["desc"] + f" (shortened to {S} steps)", "N": N, "nnz": inst.nnz,
+                   "replicas": R, "md_steps": S,
                    "n_ambivalent": n, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas only, {ws} GPU(s)"},
         "variants": {k: {"spin_updates_per_s": su_step * args.steps / sum(v["t_pipe"]),
@@ -442,6 +446,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="er800", choices=sorted(CONFIGS))
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--md-steps", type=int, default=0,
+                    help="override the workload's MD step count (shorter runs for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
