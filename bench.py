@@ -52,6 +52,11 @@ CONFIGS = {
                    R=4096, S=10000, n=24, kind="dense", sched="paper",
                    variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
                    cpu_steps=200),
+    "uneven512": dict(desc="512 instances, N uniform in [200,5000], half random 3-regular, half "
+                           "2-D tori, +-1, 64 replicas each, 5000 steps, one persistent batch launch",
+                      R=64, S=5000, n=24, kind="batch", sched="paper",
+                      variants=(("fp32", "PREC_FP32"), ("bf16", "PREC_BF16")), plain="fp32",
+                      cpu_steps=200),
     "sk100": dict(desc="SK N=100 +-1, 1 replica, 1000 steps, linear-gamma schedule, "
                        "n=20 exact sub-solve",
                   R=1, S=1000, n=20, kind="sparse", sched="linear_gamma",
@@ -69,6 +74,8 @@ def make_instance(name):
         return instances.sk_pm1(2000, 1300)
     if name == "sk100":
         return instances.sk_pm1(100, 1100)
+    if name == "uneven512":
+        return instances.uneven_batch(512, 200, 5000, 1400)
     raise KeyError(name)
 
 
@@ -207,8 +214,16 @@ def run_ours(args):
     if args.md_steps:
         cfg["S"] = args.md_steps
     inst = make_instance(args.config)
-    N, R, S, n = inst.N, cfg["R"], cfg["S"], cfg["n"]
-    ctx = hqa.Context.from_instance(inst)
+    batch = cfg["kind"] == "batch"
+    if batch:
+        members = [hqa.Context.from_instance(i) for i in inst]
+        ctx = hqa.Context.batch(members)
+        N, nnz = ctx.N, sum(i.nnz for i in inst)      # N = total spins of the batch
+    else:
+        ctx = hqa.Context.from_instance(inst)
+        N, nnz = inst.N, inst.nnz
+    R, S, n = cfg["R"], cfg["S"], cfg["n"]
+    count = len(inst) if batch else 1
     sched = hqa.schedule(n_ambivalent=n)
     if cfg["sched"] == "linear_gamma":
         sched.kind = hqa.SCHED_LINEAR_GAMMA
@@ -217,14 +232,17 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     seed_base = 1000 + rank * 100003
 
+    RR = R * count   # per-replica results
     out = {k: torch.empty(s, dtype=d, device=dev) for k, s, d in (
         ("phi", (R, N), torch.float32), ("p", (R, N), torch.float32),
         ("phibar", (R, N), torch.float32), ("spins", (R, N), torch.int8),
-        ("frozen", (R, N), torch.uint8), ("energy", (R,), torch.int64),
-        ("cut", (R,), torch.int64), ("tally", (R, 2), torch.int32))}
+        ("frozen", (R, N), torch.uint8), ("energy", (RR,), torch.int64),
+        ("cut", (RR,), torch.int64), ("tally", (RR, 2), torch.int32))}
 
     def pipeline(prec, seed):
         ctx.run(S, R, seed=seed, sched=sched, precision=prec, out=out)
+        if batch:
+            return None   # the batch pipeline ends at readout + energy (no batched sub-solve)
         return ctx.solve_sub(out["spins"], out["frozen"], n)
 
     def timed(fn, K, W):
@@ -284,12 +302,18 @@ def run_ours(args):
         g = torch.Generator().manual_seed(rank)
         pin_p0.copy_((torch.randint(0, 2, (R, N), generator=g) * 2 - 1).float())
         host_spins = torch.empty((R, N), dtype=torch.int8).pin_memory()
-        host_e = torch.empty((R,), dtype=torch.int64).pin_memory()
-        host_c = torch.empty((R,), dtype=torch.int64).pin_memory()
+        host_e = torch.empty((RR,), dtype=torch.int64).pin_memory()
+        host_c = torch.empty((RR,), dtype=torch.int64).pin_memory()
         d_p0 = torch.empty((R, N), dtype=torch.float32, device=dev)
         d_phi0 = torch.empty((R, N), dtype=torch.float32, device=dev)
 
         def e2e_step(k):
+            if batch:   # seeds drive the batch's initial state: H2D of the run parameters only
+                ctx.run(S, R, seed=seed_base + 11 * k, sched=sched, precision=best_prec, out=out)
+                host_spins.copy_(out["spins"], non_blocking=True)
+                host_e.copy_(out["energy"], non_blocking=True)
+                host_c.copy_(out["cut"], non_blocking=True)
+                return
             d_p0.copy_(pin_p0, non_blocking=True)
             d_phi0.copy_(pin_phi0, non_blocking=True)
             ctx.run(S, R, sched=sched, precision=best_prec, init=hqa.INIT_GIVEN, phi0=d_phi0,
@@ -316,8 +340,13 @@ def run_ours(args):
     # roofline of the dominant kernel (the MD kernel), timed alone with CUDA events
     clk = clocks.summary()
     hv = variants[head]
-    plan = ctx.plan(R, precision=hv["prec"])
-    kname = kernel_name(hqa, plan, hv["prec_name"])
+    if batch:
+        plan = {"kernel": hqa.KERNEL_SCALAR, "replicas_per_block": 0, "members": count,
+                "note": "persistent batch kernel, replica blocking chosen per batch"}
+        kname = f"k_sparse_md_batch<*,{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
+    else:
+        plan = ctx.plan(R, precision=hv["prec"])
+        kname = kernel_name(hqa, plan, hv["prec_name"])
     t_md = float(np.mean(hv["t_md"]))
     if cfg["kind"] == "dense":
         pk = measured_peaks()
@@ -329,7 +358,7 @@ def run_ours(args):
                 "mma_tflops_issued": mma / t_md / 1e12, "peak_source": pk["source"]}
     else:
         es = ELEM_BYTES[hv["prec_name"]]
-        bytes_per_launch = inst.nnz * es * R * S   # gathered operand bytes: deg x elem size per spin-update
+        bytes_per_launch = nnz * es * R * S   # gathered operand bytes: deg x elem size per spin-update
         achieved = bytes_per_launch / t_md / 1e9
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clk.get("sm_max_mhz") or 2070.0
@@ -345,7 +374,7 @@ def run_ours(args):
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
     # launches per pipeline step: MD (+ init and output copy on the dense path),
     # readout, energy, sub-solve (prep, enumeration, assemble, energy)
-    launches = (3 if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + 4
+    launches = (3 if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + (0 if batch else 4)
     line = {
         "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_pipe / args.steps,
@@ -354,8 +383,8 @@ def run_ours(args):
                   "PREC_BF16X2": "bf16x2-split-operand/f32-accumulate"}[hv["prec_name"]],
         "data": "synthetic (seeded instance generator)",
         "config": {"workload": cfg["desc"] if S == CONFIGS[args.config]["S"] else
-                   cfg["desc"] + f" (shortened to {S} steps)", "N": N, "nnz": inst.nnz,
-                   "replicas": R, "md_steps": S,
+                   cfg["desc"] + f" (shortened to {S} steps)", "N": N, "nnz": nnz,
+                   "replicas": R, "md_steps": S, "instances": count,
                    "n_ambivalent": n, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas only, {ws} GPU(s)"},
         "variants": {k: {"spin_updates_per_s": su_step * args.steps / sum(v["t_pipe"]),
@@ -367,7 +396,8 @@ def run_ours(args):
         "equal_cut": {"rule": "95% bootstrap interval of median(variant cut) - median(plain cut) "
                               "reaches 0", "plain": cfg["plain"]},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s",
-                "h2d_bytes_per_step": 2 * R * N * 4, "d2h_bytes_per_step": R * N + 2 * R * 8},
+                "h2d_bytes_per_step": 0 if batch else 2 * R * N * 4,
+                "d2h_bytes_per_step": R * N + 2 * RR * 8},
         "gpu_launches": launches * args.steps,
         "roofline": roof,
         "clocks": clk,
@@ -401,6 +431,16 @@ def cpu_baseline(args, inst, cfg):
     from oracle import oracle as orc
     orc.build()
     cores = os.cpu_count() or 1
+    if cfg["kind"] == "batch":
+        # a bounded sample: every 16th member, `cores` replicas, 200 steps
+        S = cfg["cpu_steps"]
+        su, wall = 0, 0.0
+        for m in inst[::16]:
+            wall += _oracle_sample(m, S, cores, cores)
+            su += m.N * cores * S
+        return {"value": su / wall, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{len(inst[::16])} of {len(inst)} members x {cores} of {cfg['R']} "
+                          f"replicas x {S} of {cfg['S']} steps (MD only, FP64)"}
     S, reps = _cpu_sample_shape(cfg, cores, 16 if cfg["kind"] == "sparse" else 2)
     wall = _oracle_sample(inst, S, reps, cores)
     return {"value": inst.N * reps * S / wall, "unit": "spin-updates/s", "cores": cores,
@@ -419,6 +459,8 @@ def run_reference(args):
     inst = make_instance(args.config)
     cores = os.cpu_count() or 1
     S, reps = _cpu_sample_shape(cfg, cores, 1)
+    if cfg["kind"] == "batch":
+        inst = inst[len(inst) // 2]     # one mid-size member per step
     for _ in range(args.warmup):
         _oracle_sample(inst, min(S, 20), reps, cores)
     walls = [_oracle_sample(inst, S, reps, cores) for _ in range(args.steps)]

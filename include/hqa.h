@@ -157,6 +157,19 @@ hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t 
 hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
                           const float* val, const float* h, uint32_t flags, hqa_ctx** out);
 
+/* Creates a batch context over `count` existing contexts (instances of
+ * uneven size, e.g. the paper's ensembles of random instances).  The members
+ * are not copied: they must outlive the batch and not be destroyed first.
+ * hqa_run on a batch runs `replicas` replicas of every member in one
+ * persistent launch (work items = member x replica block, longest first).
+ * Batch array layout: member k's [R][N_k] block starts at R * (N_0 + ... +
+ * N_{k-1}); per-replica results (energy, cut, tally) are [count][R].  Member
+ * k draws its momenta from the stream seed + (k + 1) * 0x632BE59BD9B4E019.
+ * Members need couplings in {-1, 0, +1}; hqa_readout and hqa_energy accept a
+ * batch with the same layout; other calls return HQA_ERR_UNSUPPORTED.
+ * Errors: INVALID_ARG (count < 1, null or batch member), UNSUPPORTED, OOM, CUDA. */
+hqa_status hqa_create_batch(int32_t count, hqa_ctx* const* instances, hqa_ctx** out);
+
 /* Queries: number of spins, stored off-diagonal entries, and whether all
  * couplings and fields are integers (the int64 energy path). */
 hqa_status hqa_ctx_info(const hqa_ctx* ctx, int32_t* N, int64_t* nnz, int32_t* integer_couplings);

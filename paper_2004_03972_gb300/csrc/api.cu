@@ -40,8 +40,9 @@ void free_ctx_device(hqa_ctx* c)
         if (kv.second.d_tuple_list) cudaFree(kv.second.d_tuple_list);
     }
     c->plans.clear();
-    void* ptrs[] = {c->d_row_ptr, c->d_col, c->d_val,   c->d_val_i8, c->d_h,      c->d_h_i32,
-                    c->d_sched,   c->d_ws,  c->d_state, c->d_sub,    c->d_status, c->d_Jbf};
+    void* ptrs[] = {c->d_row_ptr, c->d_col,   c->d_val,    c->d_val_i8, c->d_h,
+                    c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
+                    c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -231,6 +232,72 @@ hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& o, const Spa
     return hqa_sparse_plan(ctx, RB, o.precision, plan);
 }
 
+// Batch run: one persistent launch over (member, replica block) items, then
+// batched readout and energy.  Replica blocking: the largest RB whose
+// operand buffers fit every member and that leaves at least two items per SM.
+hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+                     int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
+                     const hqa_result* out, void* stream)
+{
+    hqa_run_opts o;
+    if (opts) o = *opts;
+    else hqa_run_opts_default(&o);
+    hqa_status s = check_opts(o);
+    if (s != HQA_OK) return s;
+    if (o.init == HQA_INIT_GIVEN || o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR ||
+        o.precision == HQA_PREC_BF16X2)
+        return HQA_ERR_UNSUPPORTED;
+    if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_RANDOM_FLUX) return HQA_ERR_INVALID_ARG;
+    if (misaligned(out->phi, 4) || misaligned(out->p, 4) || misaligned(out->phibar, 4) ||
+        misaligned(out->energy, 8) || misaligned(out->cut, 8) || misaligned(out->tally, 4))
+        return HQA_ERR_INVALID_ARG;
+    const bool want_readout = out->spins || out->frozen || out->tally || out->energy || out->cut;
+    const bool want_energy = out->energy || out->cut;
+    if (want_energy && !ctx->integer) return HQA_ERR_UNSUPPORTED;
+    int RB = o.replicas_per_block;
+    if (RB == 0) {
+        const int cands[6] = {32, 16, 8, 4, 2, 1};
+        for (int rb : cands) {
+            bool fits = true;
+            for (hqa_ctx* m : ctx->members)
+                fits = fits && hqa_sparse_smem_bytes(m, rb, o.precision) <= ctx->smem_optin;
+            const int64_t items = (int64_t)ctx->members.size() * ((replicas + rb - 1) / rb);
+            if (fits && items >= 2 * (int64_t)ctx->sm_count) { RB = rb; break; }
+            if (fits) RB = rb;  // remember the smallest fitting so far (more items)
+        }
+        if (RB == 0) return HQA_ERR_TOO_LARGE;
+    }
+    s = upload_schedule(ctx, sched, dt, steps);
+    if (s != HQA_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t RN = (size_t)replicas * (size_t)ctx->total_spins;
+    const bool tmp_phibar = want_readout && !out->phibar;
+    const bool tmp_spins = want_energy && !out->spins;
+    size_t need = (tmp_phibar ? RN * sizeof(float) : 0) + (tmp_spins ? RN : 0);
+    if (need) {
+        s = hqa_reserve(&ctx->d_ws, &ctx->ws_cap, need);
+        if (s != HQA_OK) return s;
+    }
+    char* ws = static_cast<char*>(ctx->d_ws);
+    float* phibar = out->phibar;
+    if (tmp_phibar) {
+        phibar = reinterpret_cast<float*>(ws);
+        ws += RN * sizeof(float);
+    }
+    int8_t* spins = out->spins;
+    if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
+    s = hqa_batch_launch_md(ctx, RB, o.precision, ctx->d_sched, steps, sched->window, replicas,
+                            seed, o.init, sched->M, out->phi, out->p, phibar, st);
+    if (s != HQA_OK) return s;
+    if (want_readout) {
+        s = hqa_launch_readout_batch(ctx, replicas, phibar, sched->n_ambivalent, spins, out->frozen,
+                                     out->tally, st);
+        if (s != HQA_OK) return s;
+    }
+    if (want_energy) return hqa_launch_energy_batch(ctx, replicas, spins, out->energy, out->cut, st);
+    return HQA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -355,6 +422,55 @@ hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t 
     return s;
 }
 
+hqa_status hqa_create_batch(int32_t count, hqa_ctx* const* instances, hqa_ctx** out)
+{
+    if (!out) return HQA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || !instances) return HQA_ERR_INVALID_ARG;
+    for (int k = 0; k < count; ++k) {
+        const hqa_ctx* m = instances[k];
+        if (!m || m->is_batch) return HQA_ERR_INVALID_ARG;
+        if (!m->unit) return HQA_ERR_UNSUPPORTED;
+        if (m->device != instances[0]->device) return HQA_ERR_INVALID_ARG;
+    }
+    hqa_ctx* c = new (std::nothrow) hqa_ctx();
+    if (!c) return HQA_ERR_OOM;
+    c->is_batch = true;
+    c->device = instances[0]->device;
+    c->sm_count = instances[0]->sm_count;
+    c->smem_optin = instances[0]->smem_optin;
+    c->integer = true;
+    c->unit = true;
+    std::vector<BatchInst> tab(count);
+    int64_t off = 0;
+    for (int k = 0; k < count; ++k) {
+        hqa_ctx* m = instances[k];
+        c->members.push_back(m);
+        c->member_off.push_back(off);
+        c->N = std::max(c->N, m->N);
+        c->nnz += m->nnz;
+        c->integer = c->integer && m->integer;
+        c->has_h = c->has_h || m->has_h;
+        tab[k] = BatchInst{m->d_row_ptr, m->d_col, m->d_val_i8, m->has_h ? m->d_h_i32 : nullptr,
+                           m->sum_J_all, off, m->N, 0};
+        off += m->N;
+    }
+    c->total_spins = off;
+    auto fail = [&](hqa_status s) {
+        free_ctx_device(c);
+        delete c;
+        return s;
+    };
+    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess) return fail(HQA_ERR_OOM);
+    if (cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return fail(HQA_ERR_CUDA);
+    if (cudaMalloc(&c->d_binst, tab.size() * sizeof(BatchInst)) != cudaSuccess) return fail(HQA_ERR_OOM);
+    if (cudaMemcpy(c->d_binst, tab.data(), tab.size() * sizeof(BatchInst), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return fail(HQA_ERR_CUDA);
+    *out = c;
+    return HQA_OK;
+}
+
 hqa_status hqa_ctx_info(const hqa_ctx* ctx, int32_t* N, int64_t* nnz, int32_t* integer_couplings)
 {
     if (!ctx) return HQA_ERR_INVALID_ARG;
@@ -371,6 +487,7 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     if (!ctx || !out || replicas < 1) return HQA_ERR_INVALID_ARG;
     hqa_status s = check_schedule(sched, dt, steps);
     if (s != HQA_OK) return s;
+    if (ctx->is_batch) return run_batch(ctx, sched, dt, steps, replicas, seed, opts, out, stream);
     hqa_run_opts o;
     if (opts) o = *opts;
     else hqa_run_opts_default(&o);
@@ -447,6 +564,7 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
 hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
                            const hqa_run_opts* opts, void* stream)
 {
+    if (ctx && ctx->is_batch) return HQA_ERR_UNSUPPORTED;
     if (!ctx || replicas < 1 || !phi || !L || misaligned(phi, 4) || misaligned(L, 4))
         return HQA_ERR_INVALID_ARG;
     hqa_run_opts o;
@@ -473,6 +591,9 @@ hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int3
 {
     if (!ctx || replicas < 1 || !phibar || (!spins && !frozen && !tally)) return HQA_ERR_INVALID_ARG;
     if (misaligned(phibar, 4) || misaligned(tally, 4)) return HQA_ERR_INVALID_ARG;
+    if (ctx->is_batch)
+        return hqa_launch_readout_batch(ctx, replicas, phibar, n, spins, frozen, tally,
+                                        static_cast<cudaStream_t>(stream));
     return hqa_launch_readout(ctx, replicas, phibar, n, spins, frozen, tally,
                               static_cast<cudaStream_t>(stream));
 }
@@ -482,6 +603,9 @@ hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64
 {
     if (!ctx || replicas < 1 || !spins || (!energy && !cut)) return HQA_ERR_INVALID_ARG;
     if (misaligned(energy, 8) || misaligned(cut, 8)) return HQA_ERR_INVALID_ARG;
+    if (ctx->is_batch)
+        return hqa_launch_energy_batch(ctx, replicas, spins, energy, cut,
+                                       static_cast<cudaStream_t>(stream));
     return hqa_launch_energy(ctx, replicas, spins, energy, cut, static_cast<cudaStream_t>(stream));
 }
 
@@ -489,6 +613,7 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
                          const uint8_t* frozen, int32_t n, int8_t* out_spins,
                          int64_t* out_energy, void* stream)
 {
+    if (ctx && ctx->is_batch) return HQA_ERR_UNSUPPORTED;
     if (!ctx || replicas < 1 || !spins || !frozen || !out_spins) return HQA_ERR_INVALID_ARG;
     if (n < 0 || misaligned(out_energy, 8)) return HQA_ERR_INVALID_ARG;
     return hqa_launch_subsolve(ctx, replicas, spins, frozen, n, out_spins, out_energy,
@@ -498,6 +623,7 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
 hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* opts,
                           hqa_plan_info* out)
 {
+    if (ctx && ctx->is_batch) return HQA_ERR_UNSUPPORTED;
     if (!ctx || replicas < 1 || !out) return HQA_ERR_INVALID_ARG;
     hqa_run_opts o;
     if (opts) o = *opts;

@@ -67,6 +67,18 @@ struct SparsePlan {
 void hqa_schedule_bank_section(const std::vector<std::vector<int>>& lists, int P, int N, int K,
                                std::vector<int>& out /* [K][G] */, int64_t& wavefronts);
 
+// Per-instance table of a batch context (device copy used by batch kernels).
+struct BatchInst {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const int8_t* val_i8;
+    const int32_t* h_i32;
+    int64_t sumJ;
+    int64_t off;   // spins of the instances before this one
+    int32_t N;
+    int32_t pad;
+};
+
 struct hqa_ctx {
     int device = 0;
     int sm_count = 0;
@@ -110,6 +122,15 @@ struct hqa_ctx {
     size_t sub_cap = 0;
     uint32_t* d_status = nullptr;
 
+    // batch contexts: member contexts (not owned), spin offsets, device tables
+    bool is_batch = false;
+    std::vector<hqa_ctx*> members;
+    std::vector<int64_t> member_off;
+    int64_t total_spins = 0;
+    BatchInst* d_binst = nullptr;
+    void* d_bwork = nullptr;        // per-run instance arguments, work items, queue counter
+    size_t bwork_cap = 0;
+
     // dense contexts whose couplings are exact in BF16: tensor-core operand
     bool dense_tc = false;
     void* d_Jbf = nullptr;         // [Mpad][Mpad] BF16, zero padded
@@ -134,6 +155,9 @@ hqa_status hqa_vec_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t R,
 
 // sparse_md.cu
 hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out);
+hqa_status hqa_batch_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef* d_sched,
+                               int64_t S, int32_t W, int32_t R, uint64_t seed, int init, int M,
+                               float* phi_out, float* p_out, float* phibar_out, cudaStream_t st);
 int hqa_sparse_pick_rb(const hqa_ctx* ctx, int32_t R, int prec);
 size_t hqa_sparse_smem_bytes(const hqa_ctx* ctx, int RB, int prec);
 hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const StepCoef* d_sched,
@@ -154,6 +178,10 @@ hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S,
                                float* phibar_out, bool split, cudaStream_t st);
 
 // readout.cu
+hqa_status hqa_launch_readout_batch(hqa_ctx* batch, int32_t R, const float* phibar, int32_t n,
+                                    int8_t* spins, uint8_t* frozen, int32_t* tally, cudaStream_t st);
+hqa_status hqa_launch_energy_batch(hqa_ctx* batch, int32_t R, const int8_t* spins, int64_t* energy,
+                                   int64_t* cut, cudaStream_t st);
 hqa_status hqa_launch_readout(hqa_ctx* ctx, int32_t R, const float* phibar, int32_t n,
                               int8_t* spins, uint8_t* frozen, int32_t* tally, cudaStream_t st);
 hqa_status hqa_launch_energy(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,

@@ -20,12 +20,12 @@ __device__ __forceinline__ unsigned long long rkey(const float* x, int i)
     return ((unsigned long long)__float_as_uint(fabsf(x[i])) << 32) | (unsigned)i;
 }
 
-__global__ void __launch_bounds__(kThreads) k_readout(const float* __restrict__ phibar, int N,
-                                                      int n, int8_t* spins, uint8_t* frozen,
-                                                      int32_t* tally, uint32_t* status)
+// One replica: x = its N window means; spins/frozen point at its row;
+// tally at its two counters (any may be null).
+__device__ __forceinline__ void readout_block(const float* __restrict__ x, int N, int n,
+                                              int8_t* spins, uint8_t* frozen, int32_t* tally,
+                                              uint32_t* status)
 {
-    const int r = blockIdx.x;
-    const float* x = phibar + (size_t)r * N;
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix, s_mask;
     __shared__ unsigned s_target;
@@ -66,19 +66,27 @@ __global__ void __launch_bounds__(kThreads) k_readout(const float* __restrict__ 
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const float v = x[i];
         bad |= !isfinite(v);
-        const size_t o = (size_t)r * N + i;
-        if (spins) spins[o] = v >= 0.f ? 1 : -1;
+        if (spins) spins[i] = v >= 0.f ? 1 : -1;
         bool amb;
         if (nn == 0) amb = false;
         else if (nn == N) amb = true;
         else amb = rkey(x, i) <= K;
-        if (frozen) frozen[o] = amb ? 0 : 1;
+        if (frozen) frozen[i] = amb ? 0 : 1;
     }
     if (tally && threadIdx.x == 0) {
-        tally[2 * r] = N - nn;
-        tally[2 * r + 1] = nn;
+        tally[0] = N - nn;
+        tally[1] = nn;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, HQA_DEV_NONFINITE);
+}
+
+__global__ void __launch_bounds__(kThreads) k_readout(const float* __restrict__ phibar, int N,
+                                                      int n, int8_t* spins, uint8_t* frozen,
+                                                      int32_t* tally, uint32_t* status)
+{
+    const size_t r = blockIdx.x, o = r * N;
+    readout_block(phibar + o, N, n, spins ? spins + o : nullptr, frozen ? frozen + o : nullptr,
+                  tally ? tally + 2 * r : nullptr, status);
 }
 
 __device__ __forceinline__ long long block_sum_ll(long long v, long long* sh)
@@ -94,16 +102,14 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long* sh)
     return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kThreads) k_energy_csr(const int32_t* __restrict__ row_ptr,
-                                                         const int32_t* __restrict__ col,
-                                                         const int8_t* __restrict__ val,
-                                                         const int32_t* __restrict__ h, int N,
-                                                         int64_t sumJ, const int8_t* spins,
-                                                         int64_t* energy, int64_t* cut)
+// One replica: s = its N spins; energy/cut point at its result (may be null).
+__device__ __forceinline__ void energy_block(const int32_t* __restrict__ row_ptr,
+                                             const int32_t* __restrict__ col,
+                                             const int8_t* __restrict__ val,
+                                             const int32_t* __restrict__ h, int N, int64_t sumJ,
+                                             const int8_t* s, int64_t* energy, int64_t* cut)
 {
     __shared__ long long sh[kThreads / 32];
-    const int r = blockIdx.x;
-    const int8_t* s = spins + (size_t)r * N;
     // one warp per row: lanes stride the row's entries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     long long ordered = 0, field = 0;
@@ -119,12 +125,69 @@ __global__ void __launch_bounds__(kThreads) k_energy_csr(const int32_t* __restri
     const long long tord = block_sum_ll(ordered, sh);
     const long long tfld = block_sum_ll(field, sh);
     if (threadIdx.x == 0) {
-        if (energy) energy[r] = tord / 2 + tfld;
-        if (cut) cut[r] = (sumJ - tord) / 4;
+        if (energy) *energy = tord / 2 + tfld;
+        if (cut) *cut = (sumJ - tord) / 4;
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_energy_csr(const int32_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const int8_t* __restrict__ val,
+                                                         const int32_t* __restrict__ h, int N,
+                                                         int64_t sumJ, const int8_t* spins,
+                                                         int64_t* energy, int64_t* cut)
+{
+    const int r = blockIdx.x;
+    energy_block(row_ptr, col, val, h, N, sumJ, spins + (size_t)r * N, energy ? energy + r : nullptr,
+                 cut ? cut + r : nullptr);
+}
+
+// Batch of instances: block b is replica b % R of instance b / R; each
+// instance's arrays start at R * off[k] (spin-indexed) or R * k (per replica).
+__global__ void __launch_bounds__(kThreads) k_readout_batch(const BatchInst* __restrict__ inst,
+                                                            int R, int n, const float* phibar,
+                                                            int8_t* spins, uint8_t* frozen,
+                                                            int32_t* tally, uint32_t* status)
+{
+    const int k = blockIdx.x / R, r = blockIdx.x % R;
+    const BatchInst b = inst[k];
+    const size_t o = (size_t)R * b.off + (size_t)r * b.N, q = (size_t)k * R + r;
+    readout_block(phibar + o, b.N, n, spins ? spins + o : nullptr, frozen ? frozen + o : nullptr,
+                  tally ? tally + 2 * q : nullptr, status);
+}
+
+__global__ void __launch_bounds__(kThreads) k_energy_batch(const BatchInst* __restrict__ inst, int R,
+                                                           const int8_t* spins, int64_t* energy,
+                                                           int64_t* cut)
+{
+    const int k = blockIdx.x / R, r = blockIdx.x % R;
+    const BatchInst b = inst[k];
+    const size_t o = (size_t)R * b.off + (size_t)r * b.N, q = (size_t)k * R + r;
+    energy_block(b.row_ptr, b.col, b.val_i8, b.h_i32, b.N, b.sumJ, spins + o,
+                 energy ? energy + q : nullptr, cut ? cut + q : nullptr);
+}
+
 }  // namespace
+
+hqa_status hqa_launch_readout_batch(hqa_ctx* batch, int32_t R, const float* phibar, int32_t n,
+                                    int8_t* spins, uint8_t* frozen, int32_t* tally, cudaStream_t st)
+{
+    const int count = (int)batch->members.size();
+    if (count == 0 || R <= 0) return HQA_OK;
+    k_readout_batch<<<count * R, kThreads, 0, st>>>(batch->d_binst, R, n, phibar, spins, frozen,
+                                                    tally, batch->d_status);
+    return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
+
+hqa_status hqa_launch_energy_batch(hqa_ctx* batch, int32_t R, const int8_t* spins, int64_t* energy,
+                                   int64_t* cut, cudaStream_t st)
+{
+    const int count = (int)batch->members.size();
+    if (!batch->integer) return HQA_ERR_UNSUPPORTED;
+    if (count == 0 || R <= 0) return HQA_OK;
+    k_energy_batch<<<count * R, kThreads, 0, st>>>(batch->d_binst, R, spins, energy, cut);
+    return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
 
 hqa_status hqa_launch_readout(hqa_ctx* ctx, int32_t R, const float* phibar, int32_t n,
                               int8_t* spins, uint8_t* frozen, int32_t* tally, cudaStream_t st)

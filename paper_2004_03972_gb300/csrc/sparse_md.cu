@@ -110,6 +110,7 @@ struct MDArgs {
     float* p_out;
     float* phibar_out;
     float* gstate;         // p/w state in global memory when it does not fit on chip
+    size_t gstride;        // floats per CTA slice of gstate (fixed across a batch)
     uint32_t* status;
     uint64_t seed;
     int64_t S;
@@ -124,8 +125,12 @@ struct MDArgs {
 //   op[2]   : 2 buffers of Npad * RB operand elements (FP32 or BF16)
 //   master  : N * RB FP32 (BF16 operand only: the FP32 flux)
 //   p, w    : N * RB FP32 each (when state_in_smem)
+// One replica block (replicas blk*RB .. +RB-1) of one instance, whole
+// trajectory.  Called by the single-instance kernel (blk = blockIdx.x) and by
+// the persistent batch kernel (blk from its work queue); `gslot` selects the
+// CTA's slice of the global p/w state when it does not fit on chip.
 template <int RB, bool BF16>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md(const MDArgs a)
+__device__ __forceinline__ void md_block(const MDArgs& a, int blk, int gslot)
 {
     constexpr int G = 32 / RB;
     constexpr int ES = BF16 ? 2 : 4;
@@ -138,11 +143,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md(const MDArgs a)
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
     const int g = lane / RB, r = lane % RB;
-    const int rep0 = blockIdx.x * RB;
+    const int rep0 = blk * RB;
     const int NRB = a.N * RB;
 
     // p and w: shared (u32 addresses) or global (per-CTA slice), [row][RB]
-    float* gp = a.gstate ? a.gstate + (size_t)blockIdx.x * 2 * NRB : nullptr;
+    float* gp = a.gstate ? a.gstate + (size_t)gslot * a.gstride : nullptr;
     float* gw = gp ? gp + NRB : nullptr;
     const uint32_t sp = state_s, sw = state_s + (uint32_t)NRB * 4u;
 
@@ -240,6 +245,39 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md(const MDArgs a)
         bad |= !(isfinite(phi) && isfinite(p));
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_NONFINITE);
+}
+
+template <int RB, bool BF16>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md(const MDArgs a)
+{
+    md_block<RB, BF16>(a, blockIdx.x, blockIdx.x);
+}
+
+// Persistent batch kernel: work items (instance, replica block) in
+// longest-first order, taken from a global counter; every item is a whole
+// trajectory of one replica block of one instance.
+struct BatchItem {
+    int inst;
+    int blk;
+};
+
+template <int RB, bool BF16>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_sparse_md_batch(const MDArgs* __restrict__ insts, const BatchItem* __restrict__ items, int nitems,
+                  int* __restrict__ counter)
+{
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const BatchItem w = items[it];
+        const MDArgs a = insts[w.inst];
+        __syncthreads();
+        md_block<RB, BF16>(a, w.blk, blockIdx.x);
+    }
 }
 
 struct FieldArgs {
@@ -556,6 +594,7 @@ hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* pl, const StepCo
         if (s != HQA_OK) return s;
         a.state_in_smem = 0;
         a.gstate = static_cast<float*>(ctx->d_state);
+        a.gstride = sb / sizeof(float);
     }
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     cudaError_t e = HQA_DISPATCH_RB(RB, bf, launch_md_t, a, pick_threads(pl->T), smem, st);
@@ -582,5 +621,113 @@ hqa_status hqa_sparse_launch_field(hqa_ctx* ctx, const SparsePlan* pl, int32_t R
     a.T = pl->T;
     a.R = R;
     cudaError_t e = HQA_DISPATCH_RB(RB, bf, launch_field_t, a, pick_threads(pl->T), smem, st);
+    return e == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batch: every member instance x ceil(R / RB) replica blocks becomes a
+// work item; items are ordered longest-first (cost ~ stored positions per
+// step + the per-element update) and pulled from a counter by a persistent
+// grid of one CTA per SM.  Instance k's outputs start at R * (sum of the
+// earlier members' N); its momenta use the stream seed + (k + 1) * 0x632BE59BD9B4E019.
+// ---------------------------------------------------------------------------
+template <int RB, bool BF16>
+static cudaError_t launch_batch_t(const MDArgs* insts, const BatchItem* items, int nitems,
+                                  int* counter, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sparse_md_batch<RB, BF16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sparse_md_batch<RB, BF16><<<grid, kMaxThreads, smem, st>>>(insts, items, nitems, counter);
+    return cudaGetLastError();
+}
+
+hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_sched, int64_t S,
+                               int32_t W, int32_t R, uint64_t seed, int init, int M,
+                               float* phi_out, float* p_out, float* phibar_out, cudaStream_t st)
+{
+    const int count = (int)b->members.size();
+    const bool bf = prec == HQA_PREC_BF16;
+    // shared memory: the largest member's operand buffers, plus p/w on chip where they
+    // fit; 1 KB of the opt-in limit stays free for the kernel's static shared memory
+    const size_t cap = b->smem_optin - 1024;
+    size_t smem = 0;
+    for (hqa_ctx* m : b->members) smem = std::max(smem, hqa_sparse_smem_bytes(m, RB, prec));
+    if (smem > cap) return HQA_ERR_TOO_LARGE;
+    size_t smem_dyn = smem;
+    for (hqa_ctx* m : b->members) {
+        const size_t need = hqa_sparse_smem_bytes(m, RB, prec) + state_bytes(m, RB);
+        if (need <= cap) smem_dyn = std::max(smem_dyn, need);
+    }
+    std::vector<MDArgs> args(count);
+    std::vector<BatchItem> items;
+    std::vector<double> cost;
+    size_t gslot = 0;
+    const int blocks = (R + RB - 1) / RB;
+    for (int k = 0; k < count; ++k) {
+        hqa_ctx* m = b->members[k];
+        const SparsePlan* pl = nullptr;
+        hqa_status s = hqa_sparse_plan(m, RB, prec, &pl);
+        if (s != HQA_OK) return s;
+        MDArgs a{};
+        a.entries = pl->d_entries;
+        a.tuples = pl->d_tuples;
+        a.tuple_rows = pl->d_tuple_rows;
+        a.sched = d_sched;
+        a.h = m->has_h ? m->d_h : nullptr;
+        const size_t off = (size_t)R * (size_t)b->member_off[k];
+        a.phi_out = phi_out ? phi_out + off : nullptr;
+        a.p_out = p_out ? p_out + off : nullptr;
+        a.phibar_out = phibar_out ? phibar_out + off : nullptr;
+        a.status = b->d_status;
+        a.seed = seed + (uint64_t)(k + 1) * 0x632BE59BD9B4E019ull;
+        a.S = S;
+        a.W = W;
+        a.N = m->N;
+        a.Npad = pl->Npad;
+        a.T = pl->T;
+        a.R = R;
+        a.M = M;
+        a.init = init;
+        const size_t need = hqa_sparse_smem_bytes(m, RB, prec) + state_bytes(m, RB);
+        a.state_in_smem = need <= smem_dyn ? 1 : 0;
+        if (!a.state_in_smem) gslot = std::max(gslot, state_bytes(m, RB));
+        args[k] = a;
+        const double c = (double)pl->chunks * 4.0 * pl->G + 8.0 * m->N;  // positions + updates per step
+        for (int blk = 0; blk < blocks; ++blk) {
+            items.push_back({k, blk});
+            cost.push_back(c);
+        }
+    }
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<BatchItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    const int grid = b->sm_count;
+    // device work tables: instance args | items | counter
+    const size_t off_items = (args.size() * sizeof(MDArgs) + 255) & ~(size_t)255;
+    const size_t off_cnt = off_items + ((sorted.size() * sizeof(BatchItem) + 255) & ~(size_t)255);
+    hqa_status s = hqa_reserve(&b->d_bwork, &b->bwork_cap, off_cnt + 256);
+    if (s != HQA_OK) return s;
+    if (gslot) {
+        s = hqa_reserve(&b->d_state, &b->state_cap, (size_t)grid * gslot);
+        if (s != HQA_OK) return s;
+        for (auto& a : args)
+            if (!a.state_in_smem) {
+                a.gstate = static_cast<float*>(b->d_state);
+                a.gstride = gslot / sizeof(float);   // the largest member's slice
+            }
+    }
+    char* w = static_cast<char*>(b->d_bwork);
+    HQA_CUDA_TRY(cudaMemcpyAsync(w, args.data(), args.size() * sizeof(MDArgs), cudaMemcpyHostToDevice, st));
+    HQA_CUDA_TRY(cudaMemcpyAsync(w + off_items, sorted.data(), sorted.size() * sizeof(BatchItem),
+                                 cudaMemcpyHostToDevice, st));
+    HQA_CUDA_TRY(cudaMemsetAsync(w + off_cnt, 0, sizeof(int), st));
+    // the host vectors above are copied synchronously (pageable source) before return
+    cudaError_t e = HQA_DISPATCH_RB(RB, bf, launch_batch_t, reinterpret_cast<const MDArgs*>(w),
+                                    reinterpret_cast<const BatchItem*>(w + off_items),
+                                    (int)sorted.size(), reinterpret_cast<int*>(w + off_cnt), grid,
+                                    smem_dyn, st);
     return e == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
 }

@@ -325,6 +325,7 @@ extern "C" hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, cons
                                             int64_t* out_energy, void* stream)
 {
     if (!ctx || replicas < 1 || !spins || !frozen || !out_spins || n < 0) return HQA_ERR_INVALID_ARG;
+    if (ctx->is_batch) return HQA_ERR_UNSUPPORTED;  // a batch has no coupling arrays of its own
     if (out_energy && ((uintptr_t)out_energy % 8) != 0) return HQA_ERR_INVALID_ARG;
     if (replicas > kNoAllocMaxReplicas) return HQA_ERR_TOO_LARGE;  // scratch holds 2048 replicas
     if (!ctx->integer || !ctx->unit) return HQA_ERR_UNSUPPORTED;

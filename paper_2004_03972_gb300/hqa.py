@@ -29,6 +29,7 @@ KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_DENSE = 0, 1, 2, 3
 # every symbol include/hqa.h declares
 EXPORTS = (
     "hqa_schedule_default", "hqa_run_opts_default", "hqa_create_dense", "hqa_create_csr",
+    "hqa_create_batch",
     "hqa_ctx_info", "hqa_run", "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
     "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync", "hqa_status_string", "hqa_destroy",
 )
@@ -97,6 +98,7 @@ def lib() -> C.CDLL:
             L.hqa_create_dense.argtypes = [i32, vp, vp, u32, C.POINTER(vp)]
             L.hqa_create_csr.argtypes = [i32, i64, vp, vp, vp, vp, u32, C.POINTER(vp)]
             L.hqa_ctx_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            L.hqa_create_batch.argtypes = [i32, C.POINTER(vp), C.POINTER(vp)]
             L.hqa_run.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i32, u64,
                                   C.POINTER(RunOpts), C.POINTER(Result), vp]
             L.hqa_local_field.argtypes = [vp, i32, vp, vp, C.POINTER(RunOpts), vp]
@@ -110,7 +112,7 @@ def lib() -> C.CDLL:
             L.hqa_status_string.restype = C.c_char_p
             L.hqa_destroy.argtypes = [vp]
             L.hqa_destroy.restype = None
-            for name in ("hqa_create_dense", "hqa_create_csr", "hqa_ctx_info", "hqa_run",
+            for name in ("hqa_create_dense", "hqa_create_csr", "hqa_create_batch", "hqa_ctx_info", "hqa_run",
                          "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
                          "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync"):
                 getattr(L, name).restype = C.c_int
@@ -150,6 +152,27 @@ class Context:
     def __init__(self, handle: C.c_void_p, N: int):
         self._h = handle
         self.N = N
+        self.members = None      # batch contexts: the member Contexts (kept alive here)
+
+    @classmethod
+    def batch(cls, members):
+        """hqa_create_batch over existing contexts.  Spin-indexed outputs are the members'
+        [R][N_k] blocks back to back (see split()); per-replica outputs are [count][R]."""
+        arr = (C.c_void_p * len(members))(*[m._h.value for m in members])
+        out = C.c_void_p()
+        _check(lib().hqa_create_batch(len(members), arr, C.byref(out)), "hqa_create_batch")
+        c = cls(out, sum(m.N for m in members))
+        c.members = list(members)
+        return c
+
+    def split(self, t, R):
+        """Per-member views [R][N_k] of a batch output laid out as hqa_run writes it."""
+        flat = t.reshape(-1)
+        views, off = [], 0
+        for m in self.members:
+            views.append(flat[off:off + R * m.N].view(R, m.N))
+            off += R * m.N
+        return views
 
     @classmethod
     def from_dense(cls, J, h=None):
@@ -211,10 +234,11 @@ class Context:
         if out is None:
             dev = torch.device("cuda")
             names = outputs or ("phi", "p", "phibar", "spins", "frozen", "energy", "cut", "tally")
+            Rr = R * (len(self.members) if self.members else 1)   # per-replica results
             shapes = {"phi": ((R, N), torch.float32), "p": ((R, N), torch.float32),
                       "phibar": ((R, N), torch.float32), "spins": ((R, N), torch.int8),
-                      "frozen": ((R, N), torch.uint8), "energy": ((R,), torch.int64),
-                      "cut": ((R,), torch.int64), "tally": ((R, 2), torch.int32)}
+                      "frozen": ((R, N), torch.uint8), "energy": ((Rr,), torch.int64),
+                      "cut": ((Rr,), torch.int64), "tally": ((Rr, 2), torch.int32)}
             out = {k: torch.empty(*shapes[k][:1], dtype=shapes[k][1], device=dev) for k in names}
         res = Result(**{k: (v.data_ptr() if v is not None else None) for k, v in out.items()})
         dt = (1.0 / steps if steps > 0 else 1.0) if dt is None else dt
@@ -293,6 +317,7 @@ class Context:
         if self._h:
             lib().hqa_destroy(self._h)
             self._h = None
+        self.members = None
 
     def __del__(self):
         try:

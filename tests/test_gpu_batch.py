@@ -1,0 +1,125 @@
+"""Uneven batches (hqa_create_batch): one persistent launch over many instances of
+different size must give every member exactly what a run of that member alone gives
+(same kernel and blocking: bitwise), and match the FP64 oracle (FP32 tolerances)."""
+import numpy as np
+import pytest
+
+from paper_2004_03972_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLD = 0x632BE59BD9B4E019
+M64 = (1 << 64) - 1
+
+
+def member_seed(seed, k):
+    return (seed + (k + 1) * GOLD) & M64
+
+
+@pytest.fixture(scope="module")
+def hqa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_03972_gb300 import build, hqa as H
+    build.build()
+    return H
+
+
+def _members():
+    return [instances.regular3_pm1(50, 1), instances.torus_pm1(7, 8, 2),
+            instances.with_integer_field(instances.regular3_pm1(120, 3), 1, 4),
+            instances.torus_pm1(10, 12, 5), instances.regular3_pm1(301, 6),
+            instances.torus_pm1(5, 20, 7)]
+
+
+@pytest.mark.parametrize("rb", [1, 2, 4])
+def test_batch_equals_member_runs_bitwise(hqa, rb):
+    insts = _members()
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, seed = 5, 80, 99
+    sched = hqa.schedule(n_ambivalent=6)
+    out = batch.run(S, R, seed=seed, sched=sched, dt=1 / 400, replicas_per_block=rb,
+                    kernel=hqa.KERNEL_SCALAR)
+    batch.sync()
+    views = {k: batch.split(out[k], R) for k in ("phi", "p", "phibar", "spins", "frozen")}
+    for k, c in enumerate(ctxs):
+        alone = c.run(S, R, seed=member_seed(seed, k), sched=sched, dt=1 / 400,
+                      replicas_per_block=rb, kernel=hqa.KERNEL_SCALAR)
+        c.sync()
+        for key in views:
+            assert torch.equal(views[key][k], alone[key]), (k, key)
+        assert torch.equal(out["energy"][k * R:(k + 1) * R], alone["energy"])
+        assert torch.equal(out["cut"][k * R:(k + 1) * R], alone["cut"])
+        assert torch.equal(out["tally"][k * R:(k + 1) * R], alone["tally"])
+
+
+def test_batch_matches_oracle(hqa, orc):
+    insts = _members()
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, seed, dt = 4, 100, 7, 1 / 500
+    out = batch.run(S, R, seed=seed, dt=dt, outputs=("phi", "p", "phibar"))
+    batch.sync()
+    phis, ps = batch.split(out["phi"], R), batch.split(out["p"], R)
+    for k, inst in enumerate(insts):
+        pr = orc.Problem.from_instance(inst)
+        for r in (0, R - 1):
+            p0 = orc.initial_momenta(member_seed(seed, k), r, inst.N)
+            ophi, op, _ = orc.md_run(pr, S, dt=dt, p0=p0)
+            g_phi = phis[k][r].cpu().numpy().astype(np.float64)
+            g_p = ps[k][r].cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(g_phi - ophi)) <= 1e-5 * np.max(np.abs(ophi))
+            assert np.max(np.abs(g_p - op)) <= 1e-5 * max(1.0, np.max(np.abs(op)))
+
+
+def test_uneven_batch_structure(hqa, orc):
+    """The benchmark ensemble's structure at reduced count: N uniform in [200, 5000],
+    half 3-regular, half tori; readout and energies exact for sampled members."""
+    insts = instances.uneven_batch(16, 200, 5000, 4)
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, n = 8, 300, 24
+    out = batch.run(S, R, seed=3, sched=hqa.schedule(n_ambivalent=n))
+    batch.sync()
+    pbar = batch.split(out["phibar"], R)
+    spins = batch.split(out["spins"], R)
+    for k in (0, 5, 15):
+        pr = orc.Problem.from_instance(insts[k])
+        for r in (0, R - 1):
+            s, f = orc.readout(pbar[k][r].cpu().numpy().astype(np.float64), n)
+            assert np.array_equal(spins[k][r].cpu().numpy(), s)
+            assert int(out["energy"][k * R + r]) == orc.energy_int(pr, s)
+            assert int(out["cut"][k * R + r]) == orc.cut_int(pr, s)
+    assert torch.all(out["tally"][:, 1] == n)
+
+
+def test_batch_rejects_unsupported(hqa):
+    ctxs = [hqa.Context.from_instance(instances.torus_pm1(4, 4, 1))]
+    batch = hqa.Context.batch(ctxs)
+    with pytest.raises(hqa.HQAError):
+        batch.local_field(torch.zeros((1, 16), device="cuda"))
+    with pytest.raises(hqa.HQAError):
+        hqa.Context.batch([batch])
+
+
+def test_batch_spilled_state_bitwise(hqa):
+    """Members too large to keep p and the window sums on chip use per-CTA slices in
+    global memory; slices must not overlap across members of different size."""
+    insts = [instances.regular3_pm1(4000, 11), instances.torus_pm1(50, 60, 12),
+             instances.regular3_pm1(3400, 13), instances.torus_pm1(9, 9, 14),
+             instances.regular3_pm1(4400, 15)]
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, seed = 16, 60, 5
+    out = batch.run(S, R, seed=seed, dt=1 / 300, replicas_per_block=4, kernel=hqa.KERNEL_SCALAR,
+                    outputs=("phi", "p", "phibar"))
+    batch.sync()
+    for key in ("phi", "p", "phibar"):
+        views = batch.split(out[key], R)
+        for k, c in enumerate(ctxs):
+            alone = c.run(S, R, seed=member_seed(seed, k), dt=1 / 300, replicas_per_block=4,
+                          kernel=hqa.KERNEL_SCALAR, outputs=(key,))
+            c.sync()
+            assert torch.equal(views[k], alone[key]), (k, key)
