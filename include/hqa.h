@@ -72,8 +72,8 @@ typedef struct {
     double hstep;                 /* h = dtau / g multiplying each kick and drift; paper: 1 */
     int32_t window;               /* W: phibar averages phi^(m), m = S-W+1..S; paper: 100 */
     int32_t n_ambivalent;         /* n: the n smallest |phibar| are ambivalent */
-    const double* table_alpha;    /* host, HQA_SCHED_TABLE only, 2*steps+1 values */
-    const double* table_beta;     /* host, HQA_SCHED_TABLE only, steps+1 values */
+    const double* table_alpha;    /* host, HQA_SCHED_TABLE only, 2*(start_step+steps)+1 values */
+    const double* table_beta;     /* host, HQA_SCHED_TABLE only, start_step+steps+1 values */
 } hqa_schedule;
 
 /* Initial conditions. */
@@ -108,6 +108,13 @@ typedef struct {
     const float* p0;            /* device [R][N]; HQA_INIT_GIVEN only */
     int32_t replicas_per_block; /* 0 = chosen by the library; else 1,2,4,8,16,32 */
     int32_t kernel;             /* HQA_KERNEL_*; default AUTO */
+    int64_t start_step;         /* resume: first step index m0 (default 0).  With m0 > 0 the
+                                   run continues a trajectory: init must be HQA_INIT_GIVEN
+                                   with phi0 = phi^(m0) and p0 = p^(m0 - 1/2) as returned by
+                                   the previous call, every kick is a full kick and step j
+                                   evaluates the schedule at tau = (m0 + j) dt.  Splitting a
+                                   run this way reproduces phi and p bitwise; phibar
+                                   averages the last W steps of this call. */
 } hqa_run_opts;
 
 /* Caller-owned device outputs of hqa_run ([R][N] unless noted).  Any
@@ -283,6 +290,39 @@ typedef struct {
 
 hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* opts,
                           hqa_plan_info* out);
+
+/* ---------------------------------------------------------------------
+ * Surrogate gate (an addition to the method: the paper has no learned
+ * component).  A per-spin MLP, 6 inputs -> 64 ReLU -> 64 ReLU -> 2 logits,
+ * predicts from features of the first part of a trajectory whether a spin
+ * ends frozen (logit 0) and whether it ends at s = +1 (logit 1).  Trained
+ * with the mean binary cross-entropy of the two sigmoid outputs.
+ * Parameter vector (HQA_MLP_PARAMS FP32 values, in this order):
+ *   W1[64][6], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+ * precision: HQA_PREC_FP32, or HQA_PREC_BF16 (weights, inputs and hidden
+ * activations rounded to BF16, FP32 accumulation).
+ * --------------------------------------------------------------------- */
+enum { HQA_MLP_IN = 6, HQA_MLP_HIDDEN = 64, HQA_MLP_OUT = 2, HQA_MLP_PARAMS = 4738 };
+
+typedef struct hqa_mlp hqa_mlp;
+
+/* Creates a network on the current device from host parameters (copied);
+ * AdamW moments start at zero. */
+hqa_status hqa_mlp_create(const float* params, hqa_mlp** out);
+/* Copies the current FP32 master parameters to host memory. */
+hqa_status hqa_mlp_params(const hqa_mlp* mlp, float* params);
+/* logits [n][2] for inputs x [n][6] (device arrays). */
+hqa_status hqa_mlp_forward(hqa_mlp* mlp, int64_t n, const float* x, float* logits,
+                           int32_t precision, void* stream);
+/* Gradient of the mean loss over n samples x [n][6], labels y [n][2] in
+ * {0, 1} (device), into grad [HQA_MLP_PARAMS] and loss [1] (device; loss
+ * may be NULL). */
+hqa_status hqa_mlp_grad(hqa_mlp* mlp, int64_t n, const float* x, const float* y, float* grad,
+                        float* loss, int32_t precision, void* stream);
+/* One AdamW step (decoupled weight decay) with device gradient `grad`. */
+hqa_status hqa_mlp_adamw(hqa_mlp* mlp, const float* grad, float lr, float beta1, float beta2,
+                         float eps, float weight_decay, void* stream);
+void hqa_mlp_destroy(hqa_mlp* mlp);
 
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */

@@ -447,3 +447,92 @@ int64_t or_subsolve(int32_t N, const double* J, const int64_t* row_ptr, const in
     free(amb); free(pos); free(Je); free(he); free(s);
     return full;
 }
+
+/* ------------------------------------------------------------------ */
+/* Surrogate MLP (a learned gate added on top of the method; the paper */
+/* has none).  6 inputs -> 64 ReLU -> 64 ReLU -> 2 logits; each logit   */
+/* is an independent sigmoid output with binary cross-entropy:          */
+/*   loss = (1/n) sum_samples sum_o [ softplus(z_o) - y_o z_o ].        */
+/* params: W1[64][6], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].     */
+/* The backward pass is the chain rule written out layer by layer.      */
+/* Returns the mean loss; grad (if not NULL) receives d loss / d params; */
+/* logits (if not NULL) receives z [n][2].                              */
+/* ------------------------------------------------------------------ */
+#define OR_MLP_IN 6
+#define OR_MLP_H 64
+#define OR_MLP_OUT 2
+
+static double softplus(double z) { return z > 0 ? z + log1p(exp(-z)) : log1p(exp(z)); }
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+double or_mlp_loss_grad(int64_t n, const double* x, const double* y, const double* params,
+                        double* grad, double* logits)
+{
+    const double* W1 = params;
+    const double* b1 = W1 + OR_MLP_H * OR_MLP_IN;
+    const double* W2 = b1 + OR_MLP_H;
+    const double* b2 = W2 + OR_MLP_H * OR_MLP_H;
+    const double* W3 = b2 + OR_MLP_H;
+    const double* b3 = W3 + OR_MLP_OUT * OR_MLP_H;
+    const int P = OR_MLP_H * OR_MLP_IN + OR_MLP_H + OR_MLP_H * OR_MLP_H + OR_MLP_H +
+                  OR_MLP_OUT * OR_MLP_H + OR_MLP_OUT;
+    double *gW1 = NULL, *gb1 = NULL, *gW2 = NULL, *gb2 = NULL, *gW3 = NULL, *gb3 = NULL;
+    if (grad) {
+        memset(grad, 0, sizeof(double) * P);
+        gW1 = grad;
+        gb1 = gW1 + OR_MLP_H * OR_MLP_IN;
+        gW2 = gb1 + OR_MLP_H;
+        gb2 = gW2 + OR_MLP_H * OR_MLP_H;
+        gW3 = gb2 + OR_MLP_H;
+        gb3 = gW3 + OR_MLP_OUT * OR_MLP_H;
+    }
+    double loss = 0.0;
+    double a1[OR_MLP_H], h1[OR_MLP_H], a2[OR_MLP_H], h2[OR_MLP_H], z[OR_MLP_OUT];
+    double dz[OR_MLP_OUT], dh2[OR_MLP_H], da2[OR_MLP_H], dh1[OR_MLP_H], da1[OR_MLP_H];
+    for (int64_t s = 0; s < n; ++s) {
+        const double* xs = x + s * OR_MLP_IN;
+        /* forward */
+        for (int k = 0; k < OR_MLP_H; ++k) {
+            a1[k] = b1[k];
+            for (int i = 0; i < OR_MLP_IN; ++i) a1[k] += W1[k * OR_MLP_IN + i] * xs[i];
+            h1[k] = a1[k] > 0 ? a1[k] : 0.0;
+        }
+        for (int j = 0; j < OR_MLP_H; ++j) {
+            a2[j] = b2[j];
+            for (int k = 0; k < OR_MLP_H; ++k) a2[j] += W2[j * OR_MLP_H + k] * h1[k];
+            h2[j] = a2[j] > 0 ? a2[j] : 0.0;
+        }
+        for (int o = 0; o < OR_MLP_OUT; ++o) {
+            z[o] = b3[o];
+            for (int j = 0; j < OR_MLP_H; ++j) z[o] += W3[o * OR_MLP_H + j] * h2[j];
+            loss += softplus(z[o]) - y[s * OR_MLP_OUT + o] * z[o];
+            if (logits) logits[s * OR_MLP_OUT + o] = z[o];
+        }
+        if (!grad) continue;
+        /* backward: d loss/d z = (sigmoid(z) - y) / n */
+        for (int o = 0; o < OR_MLP_OUT; ++o) dz[o] = (sigmoid(z[o]) - y[s * OR_MLP_OUT + o]) / (double)n;
+        for (int j = 0; j < OR_MLP_H; ++j) {
+            dh2[j] = 0.0;
+            for (int o = 0; o < OR_MLP_OUT; ++o) dh2[j] += W3[o * OR_MLP_H + j] * dz[o];
+            da2[j] = a2[j] > 0 ? dh2[j] : 0.0;
+        }
+        for (int k = 0; k < OR_MLP_H; ++k) {
+            dh1[k] = 0.0;
+            for (int j = 0; j < OR_MLP_H; ++j) dh1[k] += W2[j * OR_MLP_H + k] * da2[j];
+            da1[k] = a1[k] > 0 ? dh1[k] : 0.0;
+        }
+        for (int o = 0; o < OR_MLP_OUT; ++o) {
+            gb3[o] += dz[o];
+            for (int j = 0; j < OR_MLP_H; ++j) gW3[o * OR_MLP_H + j] += dz[o] * h2[j];
+        }
+        for (int j = 0; j < OR_MLP_H; ++j) {
+            gb2[j] += da2[j];
+            for (int k = 0; k < OR_MLP_H; ++k) gW2[j * OR_MLP_H + k] += da2[j] * h1[k];
+        }
+        for (int k = 0; k < OR_MLP_H; ++k) {
+            gb1[k] += da1[k];
+            for (int i = 0; i < OR_MLP_IN; ++i) gW1[k * OR_MLP_IN + i] += da1[k] * xs[i];
+        }
+    }
+    return loss / (double)n;
+}

@@ -75,6 +75,8 @@ def _load():
             lib.or_brute_force.restype = i64
             lib.or_subsolve.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.or_subsolve.restype = i64
+            lib.or_mlp_loss_grad.argtypes = [i64, vp, vp, vp, vp, vp]
+            lib.or_mlp_loss_grad.restype = d
             _lib = lib
     return _lib
 
@@ -234,3 +236,19 @@ def subsolve(pr: Problem, spins, frozen):
     e = _load().or_subsolve(*pr.args(), _ptr(spins), _ptr(frozen), _ptr(out), C.byref(x),
                             C.byref(em))
     return out, int(e), int(x.value), int(em.value)
+
+
+MLP_IN, MLP_H, MLP_OUT = 6, 64, 2
+MLP_P = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT
+
+
+def mlp_loss_grad(x, y, params, want_grad=True):
+    """Surrogate MLP: mean BCE loss, gradient [P] and logits [n][2] (FP64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    n = x.shape[0]
+    g = np.empty(MLP_P) if want_grad else None
+    z = np.empty((n, MLP_OUT))
+    loss = _load().or_mlp_loss_grad(n, _ptr(x), _ptr(y), _ptr(params), _ptr(g), _ptr(z))
+    return float(loss), g, z

@@ -155,10 +155,11 @@ hqa_status check_schedule(const hqa_schedule* s, double dt, int64_t steps)
 // Kick/drift coefficients per step (Methods, "Leapfrog algorithm"):
 //   kA_j = c_j h alpha(j dt) M, kB_j = c_j h beta(j dt), dA_j = h alpha((j+1/2) dt),
 // c_0 = 1/2 (initial half step), c_j = 1 after.  Computed in FP64, stored FP32.
-hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t S)
+hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t S, int64_t m0 = 0)
 {
     std::vector<StepCoef> t((size_t)S);
-    for (int64_t j = 0; j < S; ++j) {
+    for (int64_t jj = 0; jj < S; ++jj) {
+        const int64_t j = m0 + jj;   // absolute step index
         double a, b, ah;
         if (s->kind == HQA_SCHED_TABLE) {
             a = s->table_alpha[2 * j];
@@ -171,10 +172,10 @@ hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t
         }
         if (!std::isfinite(a) || !std::isfinite(ah) || !std::isfinite(b)) return HQA_ERR_INVALID_ARG;
         const double cj = j == 0 ? 0.5 : 1.0;
-        t[j].kA = (float)(cj * s->hstep * a * (double)s->M);
-        t[j].kB = (float)(cj * s->hstep * b);
-        t[j].dA = (float)(s->hstep * ah);
-        t[j].pad = 0.f;
+        t[jj].kA = (float)(cj * s->hstep * a * (double)s->M);
+        t[jj].kB = (float)(cj * s->hstep * b);
+        t[jj].dA = (float)(s->hstep * ah);
+        t[jj].pad = 0.f;
     }
     const size_t bytes = t.size() * sizeof(StepCoef);
     if (c->sched_host.size() == t.size() && c->d_sched &&
@@ -495,6 +496,7 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     if (s != HQA_OK) return s;
     if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_GIVEN) return HQA_ERR_INVALID_ARG;
     if (o.init == HQA_INIT_GIVEN && (!o.phi0 || !o.p0)) return HQA_ERR_INVALID_ARG;
+    if (o.start_step < 0 || (o.start_step > 0 && o.init != HQA_INIT_GIVEN)) return HQA_ERR_INVALID_ARG;
     if (misaligned(out->phi, 4) || misaligned(out->p, 4) || misaligned(out->phibar, 4) ||
         misaligned(out->energy, 8) || misaligned(out->cut, 8) || misaligned(out->tally, 4) ||
         misaligned(o.phi0, 4) || misaligned(o.p0, 4))
@@ -515,7 +517,7 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
         s = choose_plan(ctx, replicas, o, &plan);
         if (s != HQA_OK) return s;
     }
-    s = upload_schedule(ctx, sched, dt, steps);
+    s = upload_schedule(ctx, sched, dt, steps, o.start_step);
     if (s != HQA_OK) return s;
 
     // temporaries for outputs the caller skipped but later stages need

@@ -32,7 +32,10 @@ EXPORTS = (
     "hqa_create_batch",
     "hqa_ctx_info", "hqa_run", "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
     "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync", "hqa_status_string", "hqa_destroy",
+    "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
+    "hqa_mlp_destroy",
 )
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
 
 class HQAError(RuntimeError):
@@ -64,6 +67,7 @@ class RunOpts(C.Structure):
         ("p0", C.c_void_p),
         ("replicas_per_block", C.c_int32),
         ("kernel", C.c_int32),
+        ("start_step", C.c_int64),
     ]
 
 
@@ -108,6 +112,17 @@ def lib() -> C.CDLL:
             L.hqa_solve_sub_noalloc.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
             L.hqa_sync.argtypes = [vp, vp]
             L.hqa_plan_query.argtypes = [vp, i32, C.POINTER(RunOpts), C.POINTER(PlanInfo)]
+            L.hqa_mlp_create.argtypes = [vp, C.POINTER(vp)]
+            L.hqa_mlp_params.argtypes = [vp, vp]
+            L.hqa_mlp_forward.argtypes = [vp, i64, vp, vp, i32, vp]
+            L.hqa_mlp_grad.argtypes = [vp, i64, vp, vp, vp, vp, i32, vp]
+            L.hqa_mlp_adamw.argtypes = [vp, vp, C.c_float, C.c_float, C.c_float, C.c_float,
+                                        C.c_float, vp]
+            L.hqa_mlp_destroy.argtypes = [vp]
+            L.hqa_mlp_destroy.restype = None
+            for name in ("hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad",
+                         "hqa_mlp_adamw"):
+                getattr(L, name).restype = C.c_int
             L.hqa_status_string.argtypes = [C.c_int]
             L.hqa_status_string.restype = C.c_char_p
             L.hqa_destroy.argtypes = [vp]
@@ -209,7 +224,7 @@ class Context:
 
     def run(self, steps, replicas, seed=0, sched=None, dt=None, precision=PREC_FP32,
             init=INIT_PAPER, phi0=None, p0=None, replicas_per_block=0, outputs=None,
-            out=None, stream=None, table=None, kernel=KERNEL_AUTO):
+            out=None, stream=None, table=None, kernel=KERNEL_AUTO, start_step=0):
         """hqa_run. Returns a dict of device tensors (phi, p, phibar, spins, frozen, energy,
         cut, tally) -- those named in ``outputs`` (default: all), or the caller's ``out``."""
         import torch
@@ -231,6 +246,7 @@ class Context:
         opts.p0 = None if p0 is None else p0.data_ptr()
         opts.replicas_per_block = replicas_per_block
         opts.kernel = kernel
+        opts.start_step = int(start_step)
         if out is None:
             dev = torch.device("cuda")
             names = outputs or ("phi", "p", "phibar", "spins", "frozen", "energy", "cut", "tally")
@@ -318,6 +334,62 @@ class Context:
             lib().hqa_destroy(self._h)
             self._h = None
         self.members = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """hqa_mlp: the surrogate gate's network (device parameters, AdamW state)."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (MLP_PARAMS,):
+            raise ValueError(f"need {MLP_PARAMS} parameters")
+        self._h = C.c_void_p()
+        _check(lib().hqa_mlp_create(p.ctypes.data, C.byref(self._h)), "hqa_mlp_create")
+
+    @staticmethod
+    def init_params(seed=0):
+        """He-style random initial parameters (host)."""
+        rng = np.random.default_rng(seed)
+        parts = [rng.normal(scale=np.sqrt(2 / MLP_IN), size=MLP_HIDDEN * MLP_IN), np.zeros(MLP_HIDDEN),
+                 rng.normal(scale=np.sqrt(2 / MLP_HIDDEN), size=MLP_HIDDEN * MLP_HIDDEN),
+                 np.zeros(MLP_HIDDEN),
+                 rng.normal(scale=np.sqrt(1 / MLP_HIDDEN), size=MLP_OUT * MLP_HIDDEN), np.zeros(MLP_OUT)]
+        return np.concatenate(parts).astype(np.float32)
+
+    def params(self):
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().hqa_mlp_params(self._h, out.ctypes.data), "hqa_mlp_params")
+        return out
+
+    def forward(self, x, precision=PREC_FP32, stream=None):
+        import torch
+        z = torch.empty((x.shape[0], MLP_OUT), dtype=torch.float32, device=x.device)
+        _check(lib().hqa_mlp_forward(self._h, x.shape[0], _ptr(x), _ptr(z), precision,
+                                     _stream_ptr(stream)), "hqa_mlp_forward")
+        return z
+
+    def grad(self, x, y, precision=PREC_FP32, stream=None):
+        import torch
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(lib().hqa_mlp_grad(self._h, x.shape[0], _ptr(x), _ptr(y), _ptr(g), _ptr(loss),
+                                  precision, _stream_ptr(stream)), "hqa_mlp_grad")
+        return g, loss
+
+    def adamw(self, g, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        _check(lib().hqa_mlp_adamw(self._h, _ptr(g), lr, beta1, beta2, eps, weight_decay,
+                                   _stream_ptr(stream)), "hqa_mlp_adamw")
+
+    def close(self):
+        if self._h:
+            lib().hqa_mlp_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

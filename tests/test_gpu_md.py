@@ -278,3 +278,20 @@ def test_nonfinite_trajectory_is_latched(hqa):
     assert ei.value.status == 7
     ctx.run(10, 2, outputs=("phi",))
     ctx.sync()   # the status was cleared
+
+
+@pytest.mark.parametrize("kernel,prec,name", [(1, 0, "er_h"), (2, 0, "er800"), (2, 1, "er800"),
+                                              (3, 1, "sk100")])
+def test_resume_is_bitwise(hqa, kernel, prec, name):
+    """Checkpoint/resume: 2 x 300 steps with the state carried over equals 600 steps."""
+    inst = _inst(name)
+    ctx = hqa.Context.from_instance(inst)
+    R, S, dt = 40, 300, 1 / 1000
+    kw = dict(dt=dt, precision=prec, kernel=kernel, outputs=("phi", "p"))
+    if kernel != 3:
+        kw["replicas_per_block"] = 8
+    full = ctx.run(2 * S, R, seed=6, **kw)
+    a = ctx.run(S, R, seed=6, **kw)
+    b = ctx.run(S, R, init=hqa.INIT_GIVEN, phi0=a["phi"], p0=a["p"], start_step=S, **kw)
+    ctx.sync()
+    assert torch.equal(full["phi"], b["phi"]) and torch.equal(full["p"], b["p"])
