@@ -324,6 +324,32 @@ hqa_status hqa_mlp_adamw(hqa_mlp* mlp, const float* grad, float lr, float beta1,
                          float eps, float weight_decay, void* stream);
 void hqa_mlp_destroy(hqa_mlp* mlp);
 
+/* Features of the first `steps` leapfrog steps of a trajectory (same
+ * schedule, dt, seed and opts as the full run), computed by running those
+ * steps as `segments` consecutive resumed runs and sampling phi and the
+ * local field L at every segment end.  features: device [R][N][6], per spin
+ *   (phi, p, mean L, variance L, window mean of phi, fraction of sign
+ *   changes of phi between consecutive samples),
+ * each z-scored over the N spins of its replica.  phi, p: device [R][N],
+ * the state after `steps` (phi^(S), p^(S-1/2)) from which the full run can
+ * resume (start_step = steps).  1 <= segments <= steps; opts->start_step
+ * must be 0. */
+hqa_status hqa_run_features(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+                            int32_t segments, int32_t replicas, uint64_t seed,
+                            const hqa_run_opts* opts, float* features, float* phi, float* p,
+                            void* stream);
+
+/* Readout driven by the network's logits ([R][N][2], device: z_f frozen,
+ * z_s spin +1): s = sgn(z_s); the n spins of least confidence
+ * c = sigmoid(z_f) |2 sigmoid(z_s) - 1| are ambivalent (ties by index);
+ * accept[r] = 1 when the expected number of wrong frozen signs,
+ * E_r = sum_frozen (1 - |2 sigmoid(z_s) - 1|) / 2, is <= max_expected_errors.
+ * spins, frozen: device [R][N]; accept (uint8), expected_errors (float):
+ * device [R], either may be NULL. */
+hqa_status hqa_surrogate_readout(hqa_ctx* ctx, int32_t replicas, const float* logits, int32_t n,
+                                 float max_expected_errors, int8_t* spins, uint8_t* frozen,
+                                 uint8_t* accept, float* expected_errors, void* stream);
+
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream);

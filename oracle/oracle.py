@@ -7,7 +7,8 @@ arguments to FP64 / int64 and calls the C routine of the same name; the
 arithmetic lives in the C file, which cites the paper section each routine
 restates.
 
-Parity status: all routines are pinned by tests/test_oracle_*.py.
+Parity status: all routines are pinned by tests/test_oracle_*.py (the surrogate
+gate's routines at the end by reductions and invariants, listed there).
 """
 from __future__ import annotations
 
@@ -252,3 +253,65 @@ def mlp_loss_grad(x, y, params, want_grad=True):
     z = np.empty((n, MLP_OUT))
     loss = _load().or_mlp_loss_grad(n, _ptr(x), _ptr(y), _ptr(params), _ptr(g), _ptr(z))
     return float(loss), g, z
+
+
+# ---------------------------------------------------------------------------
+# Surrogate gate (an addition to the method: the paper has no learned part).
+# Plain compositions of the pinned routines above.  Parity pins:
+#   surrogate_features  segments = 1 reduces to (phi, p, J.phi, 0, phibar, 0) of one
+#                       md_run; Z2 covariance at h = 0; z-scored columns have mean 0, var 1
+#   surrogate_readout   sigma(z_f) = 1 reduces to the method's readout on z_s; z_s = 0
+#                       gives (N - n) / 2 expected errors
+# ---------------------------------------------------------------------------
+def segment_lengths(steps, segments):
+    """The first steps % segments segments are one step longer."""
+    return [steps // segments + (1 if k < steps % segments else 0) for k in range(segments)]
+
+
+def surrogate_features_raw(pr: Problem, steps, segments, p0, dt, window=100, M=6, kind=PAPER,
+                           prm=None, phi0=None):
+    """One replica, [N][6] before z-scoring: phi and p after `steps` steps, mean and
+    (population) variance of the local field L = J.phi + 2h|phi| over the states at the
+    segment ends, the window mean over the last min(window, last segment) steps, and
+    the fraction of consecutive segment-end states between which sgn(phi) changed
+    (sgn(0) = +1).  Every segment-end state is an independent md_run from the start."""
+    lens = segment_lengths(int(steps), int(segments))
+    ends = np.cumsum(lens)
+    Ls, sg = [], []
+    for k, m in enumerate(ends):
+        last = k == len(ends) - 1
+        phi, p, pbar = md_run(pr, int(m), dt=dt, phi0=phi0, p0=p0, kind=kind, prm=prm, M=M,
+                              window=min(window, lens[-1]) if last else window)
+        Ls.append(beta_field(pr, phi))
+        sg.append(np.where(phi >= 0, 1.0, -1.0))
+    Ls = np.array(Ls)
+    mean_L = Ls.mean(axis=0)
+    var_L = np.maximum((Ls ** 2).mean(axis=0) - mean_L ** 2, 0.0)
+    sg = np.array(sg)
+    flips = (sg[1:] != sg[:-1]).sum(axis=0) / max(len(ends) - 1, 1)
+    return np.stack([phi, p, mean_L, var_L, pbar, flips], axis=1)
+
+
+def zscore(f):
+    """Each column over the rows: (f - mean) / population std; a column with
+    variance <= 1e-20 maps to 0."""
+    mu = f.mean(axis=0)
+    var = (f ** 2).mean(axis=0) - mu ** 2
+    inv = np.where(var > 1e-20, 1.0 / np.sqrt(np.maximum(var, 1e-300)), 0.0)
+    return (f - mu) * inv
+
+
+def surrogate_readout(logits, n, max_expected_errors):
+    """logits [N][2] = (z_f, z_s) of one replica.  Spins sgn(z_s) (sgn(0) = +1); the
+    n spins with the smallest confidence sigma(z_f) |2 sigma(z_s) - 1| are ambivalent
+    (ties by index); expected wrong frozen signs E = sum_frozen (1 - |2 sigma(z_s) - 1|)/2.
+    Returns (spins, frozen, accept, E)."""
+    z = np.asarray(logits, dtype=np.float64)
+    sig = lambda t: 1.0 / (1.0 + np.exp(-t))
+    conf = sig(z[:, 0]) * np.abs(2.0 * sig(z[:, 1]) - 1.0)
+    spins = np.where(z[:, 1] >= 0, 1, -1).astype(np.int8)
+    order = np.lexsort((np.arange(len(conf)), conf))
+    frozen = np.ones(len(conf), np.uint8)
+    frozen[order[:max(0, min(int(n), len(conf)))]] = 0
+    E = float(np.sum(frozen * 0.5 * (1.0 - np.abs(2.0 * sig(z[:, 1]) - 1.0))))
+    return spins, frozen, E <= max_expected_errors, E

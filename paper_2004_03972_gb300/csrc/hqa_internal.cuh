@@ -120,6 +120,8 @@ struct hqa_ctx {
     size_t state_cap = 0;
     void* d_sub = nullptr;
     size_t sub_cap = 0;
+    void* d_feat = nullptr;         // surrogate features / readout scratch
+    size_t feat_cap = 0;
     uint32_t* d_status = nullptr;
 
     // batch contexts: member contexts (not owned), spin offsets, device tables

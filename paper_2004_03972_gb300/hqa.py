@@ -33,7 +33,7 @@ EXPORTS = (
     "hqa_ctx_info", "hqa_run", "hqa_local_field", "hqa_readout", "hqa_energy", "hqa_solve_sub",
     "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync", "hqa_status_string", "hqa_destroy",
     "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
-    "hqa_mlp_destroy",
+    "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -118,6 +118,11 @@ def lib() -> C.CDLL:
             L.hqa_mlp_grad.argtypes = [vp, i64, vp, vp, vp, vp, i32, vp]
             L.hqa_mlp_adamw.argtypes = [vp, vp, C.c_float, C.c_float, C.c_float, C.c_float,
                                         C.c_float, vp]
+            L.hqa_run_features.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i32, i32, u64,
+                                           C.POINTER(RunOpts), vp, vp, vp, vp]
+            L.hqa_run_features.restype = C.c_int
+            L.hqa_surrogate_readout.argtypes = [vp, i32, vp, i32, C.c_float, vp, vp, vp, vp, vp]
+            L.hqa_surrogate_readout.restype = C.c_int
             L.hqa_mlp_destroy.argtypes = [vp]
             L.hqa_mlp_destroy.restype = None
             for name in ("hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad",
@@ -325,6 +330,40 @@ class Context:
         _check(lib().hqa_plan_query(self._h, int(replicas), C.byref(opts), C.byref(info)),
                "hqa_plan_query")
         return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+    def features(self, steps, replicas, seed=0, sched=None, dt=None, segments=10,
+                 precision=PREC_FP32, replicas_per_block=0, kernel=KERNEL_AUTO, stream=None):
+        """hqa_run_features: ([R*N, 6] features, phi [R][N], p [R][N]) after `steps` steps."""
+        import torch
+        R, N = int(replicas), self.N
+        sched = sched if sched is not None else schedule()
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        opts.replicas_per_block = replicas_per_block
+        opts.kernel = kernel
+        dev = torch.device("cuda")
+        feat = torch.empty((R * N, MLP_IN), dtype=torch.float32, device=dev)
+        phi = torch.empty((R, N), dtype=torch.float32, device=dev)
+        p = torch.empty((R, N), dtype=torch.float32, device=dev)
+        _check(lib().hqa_run_features(self._h, C.byref(sched), float(dt), int(steps), int(segments),
+                                      R, int(seed), C.byref(opts), _ptr(feat), _ptr(phi), _ptr(p),
+                                      _stream_ptr(stream)), "hqa_run_features")
+        return feat, phi, p
+
+    def surrogate_readout(self, logits, replicas, n, max_expected_errors=1.0, stream=None):
+        """hqa_surrogate_readout: spins, frozen, accept [R] (uint8), expected errors [R]."""
+        import torch
+        R, N = int(replicas), self.N
+        dev = logits.device
+        spins = torch.empty((R, N), dtype=torch.int8, device=dev)
+        frozen = torch.empty((R, N), dtype=torch.uint8, device=dev)
+        acc = torch.empty(R, dtype=torch.uint8, device=dev)
+        err = torch.empty(R, dtype=torch.float32, device=dev)
+        _check(lib().hqa_surrogate_readout(self._h, R, _ptr(logits), int(n), float(max_expected_errors),
+                                           _ptr(spins), _ptr(frozen), _ptr(acc), _ptr(err),
+                                           _stream_ptr(stream)), "hqa_surrogate_readout")
+        return spins, frozen, acc, err
 
     def sync(self, stream=None):
         _check(lib().hqa_sync(self._h, _stream_ptr(stream)), "hqa_sync (latched device status)")

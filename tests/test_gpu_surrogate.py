@@ -1,0 +1,174 @@
+"""Surrogate gate on the GPU: features of a trajectory prefix and the confidence
+readout against the oracle, and what the trained network gains over the method
+without it, judged by the full MD run.
+
+Tolerances: the features are z-scored states after <= 100 FP32 steps (states agree
+to 1e-5 of their scale), so z-scored values agree to 2e-3 absolute; the flip
+fraction is compared on spins whose sampled fluxes all stay clear of zero.  The
+readout: spins bit-exact, the ambivalent set equal up to confidence ties within
+1e-5 relative, expected errors to 1e-4 relative."""
+import numpy as np
+import pytest
+
+from paper_2004_03972_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hqa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_03972_gb300 import build, hqa as H
+    build.build()
+    return H
+
+
+@pytest.mark.parametrize("name,steps,segments", [("er_h", 100, 5), ("torus", 97, 4),
+                                                 ("er", 60, 1)])
+def test_features_match_oracle(hqa, orc, name, steps, segments):
+    inst = {"er_h": instances.with_integer_field(instances.er_pm1(300, 0.05, 5), 2, 9),
+            "torus": instances.torus_pm1(13, 11, 2),
+            "er": instances.er_mean_degree_pm1(500, 8.0, 3)}[name]
+    ctx = hqa.Context.from_instance(inst)
+    R, seed, dt = 5, 31, 1.0 / 1000
+    sched = hqa.schedule()
+    feat, phi, p = ctx.features(steps, R, seed=seed, sched=sched, dt=dt, segments=segments)
+    ctx.sync()
+    feat = feat.cpu().numpy().reshape(R, inst.N, 6).astype(np.float64)
+    pr = orc.Problem.from_instance(inst)
+    lens = orc.segment_lengths(steps, segments)
+    for r in range(R):
+        p0 = orc.initial_momenta(seed, r, inst.N)
+        raw = orc.surrogate_features_raw(pr, steps, segments, p0, dt=dt, window=sched.window)
+        ref = orc.zscore(raw)
+        assert np.max(np.abs(feat[r, :, :5] - ref[:, :5])) <= 2e-3
+        # flip fraction: only spins whose sampled fluxes are clear of zero
+        ends = np.cumsum(lens)
+        samples = np.array([orc.md_run(pr, int(m), dt=dt, p0=p0)[0] for m in ends])
+        clear = np.all(np.abs(samples) > 1e-4 * np.abs(samples).max(), axis=0)
+        assert clear.mean() > 0.95
+        assert np.max(np.abs(feat[r, clear, 5] - ref[clear, 5])) <= 2e-3
+    # the returned state is the prefix state (resume point)
+    ophi, op, _ = orc.md_run(pr, steps, dt=dt, p0=orc.initial_momenta(seed, 0, inst.N))
+    assert np.max(np.abs(phi[0].cpu().numpy() - ophi)) <= 1e-5 * np.abs(ophi).max()
+
+
+def test_features_resume_matches_full_run(hqa):
+    """Resuming from the returned state to the full length gives the full run bitwise."""
+    inst = instances.er_mean_degree_pm1(1200, 8.0, 4)
+    ctx = hqa.Context.from_instance(inst)
+    R, S, Sc = 16, 1000, 100
+    sched = hqa.schedule()
+    full = ctx.run(S, R, seed=2, sched=sched, dt=1.0 / S, outputs=("phi", "p", "phibar"))
+    _, phi, p = ctx.features(Sc, R, seed=2, sched=sched, dt=1.0 / S, segments=10)
+    rest = ctx.run(S - Sc, R, sched=sched, dt=1.0 / S, init=hqa.INIT_GIVEN, phi0=phi, p0=p,
+                   start_step=Sc, outputs=("phi", "p", "phibar"))
+    for k in ("phi", "p", "phibar"):
+        assert torch.equal(full[k], rest[k]), k
+
+
+@pytest.mark.parametrize("n,max_err", [(0, 5.0), (24, 40.0), (300, 1e9)])
+def test_surrogate_readout_matches_oracle(hqa, orc, n, max_err):
+    inst = instances.er_mean_degree_pm1(700, 8.0, 6)
+    ctx = hqa.Context.from_instance(inst)
+    R, N = 9, inst.N
+    g = torch.Generator().manual_seed(n)
+    z = (torch.randn(R, N, 2, generator=g) * torch.tensor([3.0, 4.0])).float()
+    z[0, :5, 1] = 0.0                       # sgn(0) = +1
+    z[1, :, 0] = -200.0                     # confidence underflows: sign still from z_s
+    s, f, acc, err = ctx.surrogate_readout(z.cuda().contiguous(), R, n, max_err)
+    ctx.sync()
+    s, f, acc, err = (t.cpu().numpy() for t in (s, f, acc, err))
+    zz = z.numpy().astype(np.float64)
+    for r in range(R):
+        rs, rf, racc, rE = orc.surrogate_readout(zz[r], n, max_err)
+        np.testing.assert_array_equal(s[r], rs)
+        if not np.array_equal(f[r], rf):
+            sig = 1 / (1 + np.exp(-zz[r]))
+            conf = sig[:, 0] * np.abs(2 * sig[:, 1] - 1)
+            amb_gpu, amb_ref = conf[f[r] == 0], conf[rf == 0]
+            # only near-ties at the boundary may differ
+            assert abs(np.max(amb_gpu) - np.max(amb_ref)) <= 1e-5 * np.max(amb_ref) + 1e-37
+            assert f[r].sum() == rf.sum()
+            continue
+        assert err[r] == pytest.approx(rE, rel=1e-4, abs=1e-4)
+        assert bool(acc[r]) == racc or abs(rE - max_err) <= 1e-4 * max(1.0, max_err)
+
+
+def _train(hqa, SG, cfg, R):
+    xs, ys = [], []
+    for k in range(4):
+        c = hqa.Context.from_instance(instances.er_mean_degree_pm1(1000 + 500 * k, 8.0, 50 + k))
+        x, y = SG.dataset(c, cfg, R, seed=10 + k)
+        xs.append(x)
+        ys.append(y)
+    mlp = hqa.MLP(hqa.MLP.init_params(0))
+    hist = SG.train(mlp, xs, ys, epochs=40)
+    assert hist[-1] < hist[0]
+    return mlp
+
+
+def test_network_gain_over_method(hqa):
+    """Trained on four instances, tested on a fifth (ER N=2000, mean degree 8, +-1).
+    At an equal MD budget of 40% of the trajectory the network's readout agrees with
+    the full run more often than the method's own readout at that point, and after
+    the exact sub-solve of 24 spins its median cut is higher.  At 10% neither
+    readout carries information on the final signs (symmetry breaking comes later
+    in the anneal): the gate accepts no replica and the gated run equals the full
+    run bitwise."""
+    from paper_2004_03972_gb300 import surrogate as SG
+    R, S = 64, 5000
+    test = hqa.Context.from_instance(instances.er_mean_degree_pm1(2000, 8.0, 99))
+    full = SG.method_run(test, SG.SurrogateConfig(steps=S), R, seed=5)
+
+    cfg = SG.SurrogateConfig(steps=S, frac=0.4)
+    mlp = _train(hqa, SG, cfg, R)
+    g = SG.gated_run(test, mlp, cfg, R, seed=5)
+    base = SG.method_run(test, cfg, R, seed=5, steps=cfg.steps_c)
+    mis_net, loss_net, _ = SG.judge(g, full)
+    mis_base, _, _ = SG.judge({"surrogate_spins": base["spins"], "surrogate_cut": base["cut"],
+                               "accept": g["accept"]}, full)
+    cut_net = g["surrogate_cut"].float().median().item()
+    cut_base = base["cut"].float().median().item()
+    print(f"\n40%: mislabel net {np.median(mis_net):.3f} method {np.median(mis_base):.3f}; "
+          f"median cut net {cut_net:.0f} method {cut_base:.0f} full "
+          f"{full['cut'].float().median().item():.0f}; median cut loss {np.median(loss_net):.0f}")
+    assert np.median(mis_net) < np.median(mis_base)
+    assert cut_net > cut_base
+
+    cfg10 = SG.SurrogateConfig(steps=S, frac=0.1)
+    mlp10 = _train(hqa, SG, cfg10, R)
+    g10 = SG.gated_run(test, mlp10, cfg10, R, seed=5)
+    mis10, _, acc10 = SG.judge(g10, full)
+    print(f"10%: mislabel net {np.median(mis10):.3f}; accepted {acc10.sum()} of {R}; "
+          f"median expected errors {g10['expected_errors'].median().item():.0f}")
+    assert np.median(mis10) > 0.4
+    assert acc10.sum() == 0
+    assert torch.equal(g10["spins"], full["spins"])
+    assert torch.equal(g10["cut"], full["cut"])
+    assert g10["md_steps"] == S * R
+
+
+def test_gate_accepts_and_is_judged(hqa):
+    """A loose threshold accepts replicas; their cut loss and mislabel rate come
+    from the full run, and rejected replicas keep the full run's result bitwise."""
+    from paper_2004_03972_gb300 import surrogate as SG
+    R, S = 32, 3000
+    test = hqa.Context.from_instance(instances.er_mean_degree_pm1(1500, 8.0, 98))
+    cfg = SG.SurrogateConfig(steps=S, frac=0.6)
+    mlp = _train(hqa, SG, cfg, R)
+    probe = SG.gated_run(test, mlp, cfg, R, seed=3)
+    cfg.max_expected_errors = float(probe["expected_errors"].median())
+    g = SG.gated_run(test, mlp, cfg, R, seed=3)
+    full = SG.method_run(test, SG.SurrogateConfig(steps=S), R, seed=3)
+    mis, loss, acc = SG.judge(g, full)
+    assert 0 < acc.sum() < R
+    assert g["md_steps"] == cfg.steps_c * R + (S - cfg.steps_c) * int((~acc).sum())
+    rej = torch.from_numpy(~acc).cuda()
+    assert torch.equal(g["spins"][rej], full["spins"][rej])
+    assert torch.equal(g["cut"][rej], full["cut"][rej])
+    assert torch.equal(g["cut"][~rej], g["surrogate_cut"][~rej])
+    print(f"\n60%, threshold {cfg.max_expected_errors:.0f}: accepted {acc.sum()} of {R}, "
+          f"mislabel {np.median(mis[acc]):.3f}, median cut loss {np.median(loss[acc]):.0f}")
