@@ -350,6 +350,50 @@ hqa_status hqa_surrogate_readout(hqa_ctx* ctx, int32_t replicas, const float* lo
                                  float max_expected_errors, int8_t* spins, uint8_t* frozen,
                                  uint8_t* accept, float* expected_errors, void* stream);
 
+/* Autotuner: times each launch shape hqa_run can use for `replicas`
+ * replicas at opts->precision (NULL = defaults) -- the scalar sparse kernel
+ * at 1, 2, 4, ..., 32 replicas per block, the vectorised one at the
+ * blockings that fill a 16-byte vector, the persistent batch kernel at
+ * 1..32 (batch contexts), the dense tensor-core kernel (dense BF16/BF16X2)
+ * -- on a probe anneal of probe_steps steps (1..100000; dt = 1/probe_steps,
+ * init PAPER), one untimed run then three between CUDA events on `stream`.
+ * The fastest is written to *best (the other fields from opts) and kept in
+ * the context: later hqa_run calls for the same replica count and precision
+ * whose opts leave kernel (AUTO) and replicas_per_block (0) open use it.
+ * table (may be NULL when table_cap = 0) receives up to table_cap entries,
+ * *table_len (may be NULL) the number of candidates; a candidate the
+ * library rejects has ms_per_step = -1.  Synchronises `stream`; the probe
+ * outputs go to a context workspace.  Errors: INVALID_ARG, UNSUPPORTED (no
+ * candidate runs, or called during a capture), OOM, CUDA, and a status a
+ * probe latched (NONFINITE, TIMEOUT). */
+typedef struct {
+    int32_t kernel;               /* HQA_KERNEL_SCALAR, _VECTOR or _DENSE */
+    int32_t replicas_per_block;   /* 0 for the dense kernel */
+    double ms_per_step;           /* mean over the timed probes; -1 = rejected */
+} hqa_tune_entry;
+hqa_status hqa_autotune(hqa_ctx* ctx, const hqa_schedule* sched, int32_t replicas,
+                        const hqa_run_opts* opts, int32_t probe_steps, hqa_run_opts* best,
+                        hqa_tune_entry* table, int32_t table_cap, int32_t* table_len,
+                        void* stream);
+
+/* CUDA-graph capture of a sequence of library calls made by this thread on
+ * `stream` (a created stream: the legacy default stream, NULL, cannot be
+ * captured).  Every call between begin and end must find what it needs
+ * already prepared by an identical earlier call without capture: launch
+ * plans, the schedule table, workspaces and batch work tables.  A call that
+ * would have to allocate, upload from the host or synchronise returns
+ * HQA_ERR_UNSUPPORTED instead (as does the dense MD, a cooperative launch);
+ * hqa_capture_end then returns the first failure of the capture and no
+ * graph.  hqa_capture_end must follow every successful hqa_capture_begin.
+ * The graph replays the same launches with the same pointers and
+ * arguments: the caller keeps those buffers alive and may change their
+ * contents between replays.  hqa_sync is not capturable. */
+typedef struct hqa_graph hqa_graph;
+hqa_status hqa_capture_begin(void* stream);
+hqa_status hqa_capture_end(void* stream, hqa_graph** out);
+hqa_status hqa_graph_launch(hqa_graph* graph, void* stream);
+void hqa_graph_destroy(hqa_graph* graph);
+
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream);

@@ -3,14 +3,42 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "hqa_internal.cuh"
 
+namespace {
+thread_local bool t_capturing = false;
+thread_local hqa_status t_capture_status = HQA_OK;
+}  // namespace
+
+bool hqa_capturing() { return t_capturing; }
+
+hqa_status hqa_capture_note(hqa_status s)
+{
+    if (t_capturing && s != HQA_OK && t_capture_status == HQA_OK) t_capture_status = s;
+    return s;
+}
+
+cudaError_t hqa_smem_attr(const void* kernel, size_t smem)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(kernel);
+    if (it != done.end() && it->second >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done[kernel] = smem;
+    return e;
+}
+
 hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes)
 {
     if (bytes <= *cap && *p) return HQA_OK;
+    if (t_capturing) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
     if (*p) {
         cudaFree(*p);
         *p = nullptr;
@@ -42,7 +70,8 @@ void free_ctx_device(hqa_ctx* c)
     c->plans.clear();
     void* ptrs[] = {c->d_row_ptr, c->d_col,   c->d_val,    c->d_val_i8, c->d_h,
                     c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
-                    c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat};
+                    c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat,
+                    c->d_tune};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -181,6 +210,7 @@ hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t
     if (c->sched_host.size() == t.size() && c->d_sched &&
         std::memcmp(c->sched_host.data(), t.data(), bytes) == 0)
         return HQA_OK;
+    if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
     if (bytes > c->sched_cap) {
         if (c->d_sched) cudaFree(c->d_sched);
         c->d_sched = nullptr;
@@ -209,8 +239,16 @@ hqa_status check_opts(const hqa_run_opts& o)
 
 // Replica blocking and kernel variant: the vectorised kernel when the
 // blocking allows it and its shared-memory image fits, else the scalar one.
-hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& o, const SparsePlan** plan)
+hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& opts, const SparsePlan** plan)
 {
+    hqa_run_opts o = opts;
+    if (o.kernel == HQA_KERNEL_AUTO && o.replicas_per_block == 0) {
+        const auto it = ctx->tuned.find({R, o.precision});
+        if (it != ctx->tuned.end()) {
+            o.kernel = it->second.first;
+            o.replicas_per_block = it->second.second;
+        }
+    }
     int RB = o.replicas_per_block;
     if (RB == 0) {
         RB = hqa_sparse_pick_rb(ctx, R, o.precision);
@@ -256,6 +294,10 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     const bool want_energy = out->energy || out->cut;
     if (want_energy && !ctx->integer) return HQA_ERR_UNSUPPORTED;
     int RB = o.replicas_per_block;
+    if (RB == 0) {
+        const auto it = ctx->tuned.find({replicas, o.precision});
+        if (it != ctx->tuned.end()) RB = it->second.second;
+    }
     if (RB == 0) {
         const int cands[6] = {32, 16, 8, 4, 2, 1};
         for (int rb : cands) {
@@ -481,7 +523,7 @@ hqa_status hqa_ctx_info(const hqa_ctx* ctx, int32_t* N, int64_t* nnz, int32_t* i
     return HQA_OK;
 }
 
-hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
                    int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
                    const hqa_result* out, void* stream)
 {
@@ -563,7 +605,14 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
     return HQA_OK;
 }
 
-hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
+hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+                   int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
+                   const hqa_result* out, void* stream)
+{
+    return hqa_capture_note(run_impl(ctx, sched, dt, steps, replicas, seed, opts, out, stream));
+}
+
+static hqa_status local_field_impl(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
                            const hqa_run_opts* opts, void* stream)
 {
     if (ctx && ctx->is_batch) return HQA_ERR_UNSUPPORTED;
@@ -588,7 +637,13 @@ hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, flo
     return hqa_sparse_launch_field(ctx, plan, replicas, phi, L, st);
 }
 
-hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
+hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
+                           const hqa_run_opts* opts, void* stream)
+{
+    return hqa_capture_note(local_field_impl(ctx, replicas, phi, L, opts, stream));
+}
+
+static hqa_status readout_impl(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
                        int8_t* spins, uint8_t* frozen, int32_t* tally, void* stream)
 {
     if (!ctx || replicas < 1 || !phibar || (!spins && !frozen && !tally)) return HQA_ERR_INVALID_ARG;
@@ -600,7 +655,13 @@ hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int3
                               static_cast<cudaStream_t>(stream));
 }
 
-hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
+hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
+                       int8_t* spins, uint8_t* frozen, int32_t* tally, void* stream)
+{
+    return hqa_capture_note(readout_impl(ctx, replicas, phibar, n, spins, frozen, tally, stream));
+}
+
+static hqa_status energy_impl(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
                       int64_t* cut, void* stream)
 {
     if (!ctx || replicas < 1 || !spins || (!energy && !cut)) return HQA_ERR_INVALID_ARG;
@@ -611,7 +672,13 @@ hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64
     return hqa_launch_energy(ctx, replicas, spins, energy, cut, static_cast<cudaStream_t>(stream));
 }
 
-hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
+                      int64_t* cut, void* stream)
+{
+    return hqa_capture_note(energy_impl(ctx, replicas, spins, energy, cut, stream));
+}
+
+static hqa_status solve_sub_impl(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
                          const uint8_t* frozen, int32_t n, int8_t* out_spins,
                          int64_t* out_energy, void* stream)
 {
@@ -620,6 +687,13 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
     if (n < 0 || misaligned(out_energy, 8)) return HQA_ERR_INVALID_ARG;
     return hqa_launch_subsolve(ctx, replicas, spins, frozen, n, out_spins, out_energy,
                                static_cast<cudaStream_t>(stream));
+}
+
+hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                         const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                         int64_t* out_energy, void* stream)
+{
+    return hqa_capture_note(solve_sub_impl(ctx, replicas, spins, frozen, n, out_spins, out_energy, stream));
 }
 
 hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* opts,
@@ -671,6 +745,7 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream)
 {
     if (!ctx) return HQA_ERR_INVALID_ARG;
+    if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
     HQA_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     uint32_t bits = 0;
     HQA_CUDA_TRY(cudaMemcpy(&bits, ctx->d_status, sizeof(bits), cudaMemcpyDeviceToHost));
@@ -696,6 +771,65 @@ const char* hqa_status_string(hqa_status s)
     case HQA_ERR_TOO_LARGE: return "size beyond a documented limit";
     }
     return "unknown status";
+}
+
+hqa_status hqa_capture_begin(void* stream)
+{
+    // the legacy default stream cannot be captured
+    if (!stream || t_capturing) return HQA_ERR_INVALID_ARG;
+    HQA_CUDA_TRY(cudaStreamBeginCapture(static_cast<cudaStream_t>(stream),
+                                        cudaStreamCaptureModeThreadLocal));
+    t_capturing = true;
+    t_capture_status = HQA_OK;
+    return HQA_OK;
+}
+
+hqa_status hqa_capture_end(void* stream, hqa_graph** out)
+{
+    if (!stream || !out || !t_capturing) return HQA_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g);
+    t_capturing = false;
+    const hqa_status first = t_capture_status;
+    t_capture_status = HQA_OK;
+    if (e != cudaSuccess || first != HQA_OK || !g) {
+        (void)cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return first != HQA_OK ? first : HQA_ERR_CUDA;
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaGraphDestroy(g);
+        return HQA_ERR_CUDA;
+    }
+    hqa_graph* h = new (std::nothrow) hqa_graph;
+    if (!h) {
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return HQA_ERR_OOM;
+    }
+    h->graph = g;
+    h->exec = x;
+    *out = h;
+    return HQA_OK;
+}
+
+hqa_status hqa_graph_launch(hqa_graph* g, void* stream)
+{
+    if (!g) return HQA_ERR_INVALID_ARG;
+    HQA_CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+    return HQA_OK;
+}
+
+void hqa_graph_destroy(hqa_graph* g)
+{
+    if (!g) return;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
 }
 
 void hqa_destroy(hqa_ctx* ctx)

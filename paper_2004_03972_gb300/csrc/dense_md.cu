@@ -241,8 +241,7 @@ hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, 
     a.R = R;
     a.KT = Kpad / BK;
     const size_t smem = field_smem<kFieldBN, kFieldStages>();
-    cudaError_t e = cudaFuncSetAttribute(k_dense_field<kFieldBN, kFieldStages>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = hqa_smem_attr((const void*)k_dense_field<kFieldBN, kFieldStages>, smem);
     if (e != cudaSuccess) return HQA_ERR_CUDA;
     const dim3 grid(ctx->Mpad / BM, Rpad / kFieldBN);
     k_dense_field<kFieldBN, kFieldStages><<<grid, 192, smem, st>>>(ctx->tmJ, tmB, a);
@@ -593,8 +592,9 @@ static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid
     constexpr int STAGES = 4;
     const size_t smem = md_smem<NH, STAGES>();
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
-    if (cudaFuncSetAttribute(k_dense_md<NH, STAGES, SPLIT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    // a cooperative launch is not captured into graphs here
+    if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
+    if (hqa_smem_attr((const void*)k_dense_md<NH, STAGES, SPLIT>, smem) != cudaSuccess)
         return HQA_ERR_CUDA;
     void* args[] = {const_cast<CUtensorMap*>(&ctx->tmJ), const_cast<CUtensorMap*>(&tmB),
                     const_cast<DenseMDArgs*>(&a)};

@@ -79,6 +79,11 @@ struct BatchInst {
     int32_t pad;
 };
 
+struct hqa_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct hqa_ctx {
     int device = 0;
     int sm_count = 0;
@@ -122,6 +127,11 @@ struct hqa_ctx {
     size_t sub_cap = 0;
     void* d_feat = nullptr;         // surrogate features / readout scratch
     size_t feat_cap = 0;
+    void* d_tune = nullptr;         // autotuner probe outputs
+    size_t tune_cap = 0;
+    // autotuned (kernel, replicas per block) per (replicas, precision); used by
+    // hqa_run when the options leave both to the library
+    std::map<std::pair<int, int>, std::pair<int, int>> tuned;
     uint32_t* d_status = nullptr;
 
     // batch contexts: member contexts (not owned), spin offsets, device tables
@@ -132,6 +142,7 @@ struct hqa_ctx {
     BatchInst* d_binst = nullptr;
     void* d_bwork = nullptr;        // per-run instance arguments, work items, queue counter
     size_t bwork_cap = 0;
+    std::vector<char> bwork_host;   // what d_bwork holds (tables are uploaded only on change)
 
     // dense contexts whose couplings are exact in BF16: tensor-core operand
     bool dense_tc = false;
@@ -142,7 +153,19 @@ struct hqa_ctx {
 
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;
 // cudaFree synchronises the device, so in-flight users are finished).
+// During a capture a needed reallocation fails with HQA_ERR_UNSUPPORTED.
 hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes);
+
+// Stream capture (hqa_capture_begin/end) of the calling thread: while it is
+// open, anything that would allocate, upload from the host or synchronise
+// returns HQA_ERR_UNSUPPORTED, and the first failure of a capturing call is
+// kept for hqa_capture_end.
+bool hqa_capturing();
+hqa_status hqa_capture_note(hqa_status s);
+
+// Raises a kernel's dynamic shared-memory limit once (not per launch, so
+// that captured launches make no attribute calls).
+cudaError_t hqa_smem_attr(const void* kernel, size_t smem);
 
 // sparse_md_vec.cu
 bool hqa_vec_supported(const hqa_ctx* ctx, int RB, int prec);

@@ -427,6 +427,8 @@ hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** ou
         *out = &it->second;
         return HQA_OK;
     }
+    // building a plan allocates and uploads: not possible inside a capture
+    if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
     const int G = 32 / RB;
     const int N = ctx->N;
     const int es = prec == HQA_PREC_BF16 ? 2 : 4;
@@ -521,8 +523,7 @@ hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** ou
 template <int RB, bool BF16>
 static cudaError_t launch_md_t(const MDArgs& a, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_md<RB, BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = hqa_smem_attr((const void*)k_sparse_md<RB, BF16>, smem);
     if (e != cudaSuccess) return e;
     const int blocks = (a.R + RB - 1) / RB;
     k_sparse_md<RB, BF16><<<blocks, threads, smem, st>>>(a);
@@ -532,8 +533,7 @@ static cudaError_t launch_md_t(const MDArgs& a, int threads, size_t smem, cudaSt
 template <int RB, bool BF16>
 static cudaError_t launch_field_t(const FieldArgs& a, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_field<RB, BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = hqa_smem_attr((const void*)k_sparse_field<RB, BF16>, smem);
     if (e != cudaSuccess) return e;
     const int blocks = (a.R + RB - 1) / RB;
     k_sparse_field<RB, BF16><<<blocks, threads, smem, st>>>(a);
@@ -635,8 +635,7 @@ template <int RB, bool BF16>
 static cudaError_t launch_batch_t(const MDArgs* insts, const BatchItem* items, int nitems,
                                   int* counter, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_md_batch<RB, BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = hqa_smem_attr((const void*)k_sparse_md_batch<RB, BF16>, smem);
     if (e != cudaSuccess) return e;
     k_sparse_md_batch<RB, BF16><<<grid, kMaxThreads, smem, st>>>(insts, items, nitems, counter);
     return cudaGetLastError();
@@ -669,7 +668,8 @@ hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_s
         const SparsePlan* pl = nullptr;
         hqa_status s = hqa_sparse_plan(m, RB, prec, &pl);
         if (s != HQA_OK) return s;
-        MDArgs a{};
+        MDArgs a;
+        std::memset(&a, 0, sizeof a);   // padding too: the table is compared bytewise
         a.entries = pl->d_entries;
         a.tuples = pl->d_tuples;
         a.tuple_rows = pl->d_tuple_rows;
@@ -708,8 +708,10 @@ hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_s
     // device work tables: instance args | items | counter
     const size_t off_items = (args.size() * sizeof(MDArgs) + 255) & ~(size_t)255;
     const size_t off_cnt = off_items + ((sorted.size() * sizeof(BatchItem) + 255) & ~(size_t)255);
+    void* const held = b->d_bwork;
     hqa_status s = hqa_reserve(&b->d_bwork, &b->bwork_cap, off_cnt + 256);
     if (s != HQA_OK) return s;
+    if (b->d_bwork != held) b->bwork_host.clear();
     if (gslot) {
         s = hqa_reserve(&b->d_state, &b->state_cap, (size_t)grid * gslot);
         if (s != HQA_OK) return s;
@@ -720,11 +722,21 @@ hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_s
             }
     }
     char* w = static_cast<char*>(b->d_bwork);
-    HQA_CUDA_TRY(cudaMemcpyAsync(w, args.data(), args.size() * sizeof(MDArgs), cudaMemcpyHostToDevice, st));
-    HQA_CUDA_TRY(cudaMemcpyAsync(w + off_items, sorted.data(), sorted.size() * sizeof(BatchItem),
-                                 cudaMemcpyHostToDevice, st));
+    // the tables are uploaded only when they differ from what the device holds (so a
+    // repeated run, and a captured one, issues no host copy); the counter is reset always
+    std::vector<char> tab(off_cnt, 0);
+    const char* ab = reinterpret_cast<const char*>(args.data());
+    const char* ib = reinterpret_cast<const char*>(sorted.data());
+    std::copy(ab, ab + args.size() * sizeof(MDArgs), tab.begin());
+    std::copy(ib, ib + sorted.size() * sizeof(BatchItem), tab.begin() + (std::ptrdiff_t)off_items);
+    if (tab != b->bwork_host) {
+        if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
+        b->bwork_host.clear();
+        // pageable source: the copy is staged before cudaMemcpyAsync returns
+        HQA_CUDA_TRY(cudaMemcpyAsync(w, tab.data(), tab.size(), cudaMemcpyHostToDevice, st));
+        b->bwork_host.swap(tab);
+    }
     HQA_CUDA_TRY(cudaMemsetAsync(w + off_cnt, 0, sizeof(int), st));
-    // the host vectors above are copied synchronously (pageable source) before return
     cudaError_t e = HQA_DISPATCH_RB(RB, bf, launch_batch_t, reinterpret_cast<const MDArgs*>(w),
                                     reinterpret_cast<const BatchItem*>(w + off_items),
                                     (int)sorted.size(), reinterpret_cast<int*>(w + off_cnt), grid,

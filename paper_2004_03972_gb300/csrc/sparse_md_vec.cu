@@ -595,6 +595,8 @@ hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out)
         *out = &it->second;
         return HQA_OK;
     }
+    // building a plan allocates and uploads: not possible inside a capture
+    if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
     const int es = prec == HQA_PREC_BF16 ? 2 : 4;
     const int V = vec_width(prec);
     const int LPR = RB / V;
@@ -813,8 +815,7 @@ hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out)
 template <int RB, bool BF16>
 static cudaError_t launch_vec_md(const VArgs& a, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_md_vec<RB, BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = hqa_smem_attr((const void*)k_sparse_md_vec<RB, BF16>, smem);
     if (e != cudaSuccess) return e;
     k_sparse_md_vec<RB, BF16><<<(a.R + RB - 1) / RB, threads, smem, st>>>(a);
     return cudaGetLastError();
@@ -823,8 +824,7 @@ static cudaError_t launch_vec_md(const VArgs& a, int threads, size_t smem, cudaS
 template <int RB, bool BF16>
 static cudaError_t launch_vec_field(const VArgs& a, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_field_vec<RB, BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = hqa_smem_attr((const void*)k_sparse_field_vec<RB, BF16>, smem);
     if (e != cudaSuccess) return e;
     k_sparse_field_vec<RB, BF16><<<(a.R + RB - 1) / RB, threads, smem, st>>>(a);
     return cudaGetLastError();

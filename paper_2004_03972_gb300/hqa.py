@@ -34,6 +34,8 @@ EXPORTS = (
     "hqa_solve_sub_noalloc", "hqa_plan_query", "hqa_sync", "hqa_status_string", "hqa_destroy",
     "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
+    "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
+    "hqa_autotune",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -77,6 +79,11 @@ class PlanInfo(C.Structure):
         ("threads", C.c_int32), ("smem_bytes", C.c_int64), ("pad_ratio", C.c_double),
         ("conflict_ratio", C.c_double), ("balance", C.c_double),
     ]
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("replicas_per_block", C.c_int32),
+                ("ms_per_step", C.c_double)]
 
 
 class Result(C.Structure):
@@ -128,6 +135,18 @@ def lib() -> C.CDLL:
             for name in ("hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad",
                          "hqa_mlp_adamw"):
                 getattr(L, name).restype = C.c_int
+            L.hqa_autotune.argtypes = [vp, C.POINTER(Schedule), i32, C.POINTER(RunOpts), i32,
+                                       C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
+                                       C.POINTER(i32), vp]
+            L.hqa_autotune.restype = C.c_int
+            L.hqa_capture_begin.argtypes = [vp]
+            L.hqa_capture_begin.restype = C.c_int
+            L.hqa_capture_end.argtypes = [vp, C.POINTER(vp)]
+            L.hqa_capture_end.restype = C.c_int
+            L.hqa_graph_launch.argtypes = [vp, vp]
+            L.hqa_graph_launch.restype = C.c_int
+            L.hqa_graph_destroy.argtypes = [vp]
+            L.hqa_graph_destroy.restype = None
             L.hqa_status_string.argtypes = [C.c_int]
             L.hqa_status_string.restype = C.c_char_p
             L.hqa_destroy.argtypes = [vp]
@@ -292,20 +311,23 @@ class Context:
                                  _ptr(tally), _stream_ptr(stream)), "hqa_readout")
         return spins, frozen, tally
 
-    def energy(self, spins, stream=None):
+    def energy(self, spins, stream=None, out=None):
         import torch
         R = spins.shape[0]
-        e = torch.empty(R, dtype=torch.int64, device=spins.device)
-        c = torch.empty(R, dtype=torch.int64, device=spins.device)
+        if out is None:
+            out = (torch.empty(R, dtype=torch.int64, device=spins.device),
+                   torch.empty(R, dtype=torch.int64, device=spins.device))
+        e, c = out
         _check(lib().hqa_energy(self._h, R, _ptr(spins), _ptr(e), _ptr(c), _stream_ptr(stream)),
                "hqa_energy")
         return e, c
 
-    def solve_sub(self, spins, frozen, n, stream=None):
+    def solve_sub(self, spins, frozen, n, stream=None, out=None):
         import torch
         R = spins.shape[0]
-        out = torch.empty_like(spins)
-        e = torch.empty(R, dtype=torch.int64, device=spins.device)
+        if out is None:
+            out = (torch.empty_like(spins), torch.empty(R, dtype=torch.int64, device=spins.device))
+        out, e = out
         _check(lib().hqa_solve_sub(self._h, R, _ptr(spins), _ptr(frozen), int(n), _ptr(out),
                                    _ptr(e), _stream_ptr(stream)), "hqa_solve_sub")
         return out, e
@@ -330,6 +352,23 @@ class Context:
         _check(lib().hqa_plan_query(self._h, int(replicas), C.byref(opts), C.byref(info)),
                "hqa_plan_query")
         return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+    def autotune(self, replicas, precision=PREC_FP32, probe_steps=64, sched=None, stream=None):
+        """hqa_autotune: (best opts as a dict, [(kernel, replicas_per_block, ms_per_step)])."""
+        sched = sched if sched is not None else schedule()
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        best = RunOpts()
+        table = (TuneEntry * 32)()
+        n = C.c_int32()
+        _check(lib().hqa_autotune(self._h, C.byref(sched), int(replicas), C.byref(opts),
+                                  int(probe_steps), C.byref(best), table, 32, C.byref(n),
+                                  _stream_ptr(stream)), "hqa_autotune")
+        rows = [(table[i].kernel, table[i].replicas_per_block, table[i].ms_per_step)
+                for i in range(min(n.value, 32))]
+        return {"kernel": best.kernel, "replicas_per_block": best.replicas_per_block,
+                "precision": best.precision}, rows
 
     def features(self, steps, replicas, seed=0, sched=None, dt=None, segments=10,
                  precision=PREC_FP32, replicas_per_block=0, kernel=KERNEL_AUTO, stream=None):
@@ -435,3 +474,49 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+class Graph:
+    """A captured sequence of library calls (hqa_capture_end); launch() replays it."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(lib().hqa_graph_launch(self._h, _stream_ptr(stream)), "hqa_graph_launch")
+
+    def close(self):
+        if self._h:
+            lib().hqa_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class capture:
+    """Context manager: library calls made inside the block on ``stream`` (a
+    torch.cuda.Stream, passed explicitly to every call, with caller-allocated
+    outputs) are captured; ``.graph`` holds the Graph afterwards.  Each call must
+    have been made once before without capture (hqa_capture_begin)."""
+
+    def __init__(self, stream):
+        self.stream = stream
+        self.graph = None
+
+    def __enter__(self):
+        _check(lib().hqa_capture_begin(_stream_ptr(self.stream)), "hqa_capture_begin")
+        return self
+
+    def __exit__(self, et, ev, tb):
+        h = C.c_void_p()
+        st = lib().hqa_capture_end(_stream_ptr(self.stream), C.byref(h))
+        if et is None:
+            _check(st, "hqa_capture_end")
+            self.graph = Graph(h)
+        elif h:
+            lib().hqa_graph_destroy(h)
+        return False

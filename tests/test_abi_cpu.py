@@ -55,16 +55,18 @@ def test_struct_layout_matches_header(tmp_path):
         " printf(\"hqa_run_opts size %zu\\n\", sizeof(hqa_run_opts));\n"
         " printf(\"hqa_result size %zu\\n\", sizeof(hqa_result));\n"
         " printf(\"hqa_plan_info size %zu\\n\", sizeof(hqa_plan_info));\n"
+        " printf(\"hqa_tune_entry size %zu\\n\", sizeof(hqa_tune_entry));\n"
         + "".join(f" P(hqa_schedule, {f})\n" for f, _ in hqa.Schedule._fields_)
         + "".join(f" P(hqa_run_opts, {f})\n" for f, _ in hqa.RunOpts._fields_)
         + "".join(f" P(hqa_result, {f})\n" for f, _ in hqa.Result._fields_)
         + "".join(f" P(hqa_plan_info, {f})\n" for f, _ in hqa.PlanInfo._fields_)
+        + "".join(f" P(hqa_tune_entry, {f})\n" for f, _ in hqa.TuneEntry._fields_)
         + " return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     table = {"hqa_schedule": hqa.Schedule, "hqa_run_opts": hqa.RunOpts, "hqa_result": hqa.Result,
-             "hqa_plan_info": hqa.PlanInfo}
+             "hqa_plan_info": hqa.PlanInfo, "hqa_tune_entry": hqa.TuneEntry}
     for line in got:
         if not line:
             continue
