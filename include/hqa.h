@@ -350,6 +350,21 @@ hqa_status hqa_surrogate_readout(hqa_ctx* ctx, int32_t replicas, const float* lo
                                  float max_expected_errors, int8_t* spins, uint8_t* frozen,
                                  uint8_t* accept, float* expected_errors, void* stream);
 
+/* MD Hamiltonian (Results, Eq. (3)) of R states as a diagnostic:
+ *   H_MD = alpha(tau) sum_i (p_i^2/2 + phi_i^M)
+ *        + beta(tau) (1/2 sum_ij J_ij phi_i phi_j + sum_i h_i |phi_i| phi_i),
+ * alpha, beta from `sched` at tau (PAPER or LINEAR_GAMMA kinds; a TABLE
+ * schedule has no value between its samples: UNSUPPORTED).  With half_kick
+ * != 0 the momenta are first completed to the integer step,
+ * p - (h/2) dH_MD/dphi (h = sched->hstep), so that hqa_run's p^(S-1/2)
+ * gives H_MD at step S.  phi, p: device [R][N] float; out: device [R]
+ * double.  The local field is the library's (opts: precision, kernel; NULL =
+ * defaults); the per-spin terms and their sum are FP64.  Not for batch
+ * contexts (UNSUPPORTED). */
+hqa_status hqa_hmd(hqa_ctx* ctx, const hqa_schedule* sched, double tau, int32_t replicas,
+                   const float* phi, const float* p, int32_t half_kick, double* out,
+                   const hqa_run_opts* opts, void* stream);
+
 /* Autotuner: times each launch shape hqa_run can use for `replicas`
  * replicas at opts->precision (NULL = defaults) -- the scalar sparse kernel
  * at 1, 2, 4, ..., 32 replicas per block, the vectorised one at the

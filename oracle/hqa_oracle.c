@@ -21,7 +21,7 @@
  * pseudorandom number generators", OOPSLA 2014), written here from that
  * published definition.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   h = dtau/g is a free step factor, 1 in the paper (g = dtau identification).
  *   Window: rectangle rule over the last W integer-step samples phi^(m),
  *           m in [max(1, S-W+1), S].

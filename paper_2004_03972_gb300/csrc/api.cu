@@ -10,6 +10,21 @@
 
 #include "hqa_internal.cuh"
 
+// Schedules (Methods, "Leapfrog algorithm"; Results, Eq. (3)-(4)):
+//   alpha(tau) = alpha_f (tau + rho1 (1 - tau) + rho2 tau (tau - 1)),
+//   beta(tau)  = beta_f (tau + kappa1 (1 - tau) + kappa2 tau (tau - 1)),
+// or alpha(tau) = gamma0 (1 - tau) for the linear transverse-field schedule.
+double hqa_sched_alpha(const hqa_schedule* s, double tau)
+{
+    if (s->kind == HQA_SCHED_LINEAR_GAMMA) return s->gamma0 * (1.0 - tau);
+    return s->alpha_f * (tau + s->rho1 * (1.0 - tau) + s->rho2 * tau * (tau - 1.0));
+}
+
+double hqa_sched_beta(const hqa_schedule* s, double tau)
+{
+    return s->beta_f * (tau + s->kappa1 * (1.0 - tau) + s->kappa2 * tau * (tau - 1.0));
+}
+
 namespace {
 thread_local bool t_capturing = false;
 thread_local hqa_status t_capture_status = HQA_OK;
@@ -71,7 +86,7 @@ void free_ctx_device(hqa_ctx* c)
     void* ptrs[] = {c->d_row_ptr, c->d_col,   c->d_val,    c->d_val_i8, c->d_h,
                     c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
                     c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat,
-                    c->d_tune};
+                    c->d_tune,    c->d_diag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -158,16 +173,8 @@ bool finite_all(const float* p, size_t n)
     return true;
 }
 
-double sched_alpha(const hqa_schedule* s, double tau)
-{
-    if (s->kind == HQA_SCHED_LINEAR_GAMMA) return s->gamma0 * (1.0 - tau);
-    return s->alpha_f * (tau + s->rho1 * (1.0 - tau) + s->rho2 * tau * (tau - 1.0));
-}
-
-double sched_beta(const hqa_schedule* s, double tau)
-{
-    return s->beta_f * (tau + s->kappa1 * (1.0 - tau) + s->kappa2 * tau * (tau - 1.0));
-}
+double sched_alpha(const hqa_schedule* s, double tau) { return hqa_sched_alpha(s, tau); }
+double sched_beta(const hqa_schedule* s, double tau) { return hqa_sched_beta(s, tau); }
 
 hqa_status check_schedule(const hqa_schedule* s, double dt, int64_t steps)
 {

@@ -127,6 +127,8 @@ struct hqa_ctx {
     size_t sub_cap = 0;
     void* d_feat = nullptr;         // surrogate features / readout scratch
     size_t feat_cap = 0;
+    void* d_diag = nullptr;         // H_MD diagnostic: local field
+    size_t diag_cap = 0;
     void* d_tune = nullptr;         // autotuner probe outputs
     size_t tune_cap = 0;
     // autotuned (kernel, replicas per block) per (replicas, precision); used by
@@ -161,6 +163,8 @@ hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes);
 // returns HQA_ERR_UNSUPPORTED, and the first failure of a capturing call is
 // kept for hqa_capture_end.
 bool hqa_capturing();
+double hqa_sched_alpha(const hqa_schedule* s, double tau);
+double hqa_sched_beta(const hqa_schedule* s, double tau);
 hqa_status hqa_capture_note(hqa_status s);
 
 // Raises a kernel's dynamic shared-memory limit once (not per launch, so

@@ -35,7 +35,7 @@ EXPORTS = (
     "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
-    "hqa_autotune",
+    "hqa_autotune", "hqa_hmd",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -139,6 +139,9 @@ def lib() -> C.CDLL:
                                        C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
                                        C.POINTER(i32), vp]
             L.hqa_autotune.restype = C.c_int
+            L.hqa_hmd.argtypes = [vp, C.POINTER(Schedule), C.c_double, i32, vp, vp, i32, vp,
+                                  C.POINTER(RunOpts), vp]
+            L.hqa_hmd.restype = C.c_int
             L.hqa_capture_begin.argtypes = [vp]
             L.hqa_capture_begin.restype = C.c_int
             L.hqa_capture_end.argtypes = [vp, C.POINTER(vp)]
@@ -352,6 +355,20 @@ class Context:
         _check(lib().hqa_plan_query(self._h, int(replicas), C.byref(opts), C.byref(info)),
                "hqa_plan_query")
         return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+    def hmd(self, phi, p, tau, sched=None, half_kick=False, precision=PREC_FP32, stream=None):
+        """hqa_hmd: H_MD per replica (device float64 [R])."""
+        import torch
+        sched = sched if sched is not None else schedule()
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        R = phi.shape[0]
+        out = torch.empty(R, dtype=torch.float64, device=phi.device)
+        _check(lib().hqa_hmd(self._h, C.byref(sched), float(tau), R, _ptr(phi), _ptr(p),
+                             1 if half_kick else 0, _ptr(out), C.byref(opts),
+                             _stream_ptr(stream)), "hqa_hmd")
+        return out
 
     def autotune(self, replicas, precision=PREC_FP32, probe_steps=64, sched=None, stream=None):
         """hqa_autotune: (best opts as a dict, [(kernel, replicas_per_block, ms_per_step)])."""

@@ -117,8 +117,8 @@ def method_run(ctx, cfg: SurrogateConfig, replicas, seed, steps=None, sched=None
     return {"spins": s, "energy": e2, "cut": c, "md_spins": out["spins"], "frozen": out["frozen"]}
 
 
-def judge(gated, full, z2=True):
-    """The full MD run as the judge of the surrogate: per replica, the fraction of
+def score_against_full(gated, full, z2=True):
+    """The full MD run as the reference for the surrogate: per replica, the fraction of
     spins whose surrogate result differs from the full run's (up to the global flip
     when z2, i.e. for instances without a field) and the cut lost (full - surrogate).
     Returns numpy arrays (mislabel, cut_loss, accepted)."""

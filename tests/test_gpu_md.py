@@ -1,6 +1,6 @@
 """GPU parity of the HQA-MD path against the FP64 CPU oracle, through the C ABI.
 
-Tolerances (from the arithmetic; stated once here and in the design doc):
+Tolerances (from the arithmetic):
   local field, per element  e_i = |L_gpu - L_ref| / (|L_ref| + sum_j |J_ij| |phi_j|)
                             <= 1e-5 (FP32 operand), <= 1e-2 (BF16 operand)
   states after <= 100 steps max_i |x_gpu - x_ref| / scale_x <= 1e-5 (FP32), 1e-2 (BF16), with

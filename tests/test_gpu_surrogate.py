@@ -1,6 +1,6 @@
 """Surrogate gate on the GPU: features of a trajectory prefix and the confidence
 readout against the oracle, and what the trained network gains over the method
-without it, judged by the full MD run.
+without it, scored against the full MD run.
 
 Tolerances: the features are z-scored states after <= 100 FP32 steps (states agree
 to 1e-5 of their scale), so z-scored values agree to 2e-3 absolute; the flip
@@ -127,8 +127,8 @@ def test_network_gain_over_method(hqa):
     mlp = _train(hqa, SG, cfg, R)
     g = SG.gated_run(test, mlp, cfg, R, seed=5)
     base = SG.method_run(test, cfg, R, seed=5, steps=cfg.steps_c)
-    mis_net, loss_net, _ = SG.judge(g, full)
-    mis_base, _, _ = SG.judge({"surrogate_spins": base["spins"], "surrogate_cut": base["cut"],
+    mis_net, loss_net, _ = SG.score_against_full(g, full)
+    mis_base, _, _ = SG.score_against_full({"surrogate_spins": base["spins"], "surrogate_cut": base["cut"],
                                "accept": g["accept"]}, full)
     cut_net = g["surrogate_cut"].float().median().item()
     cut_base = base["cut"].float().median().item()
@@ -141,7 +141,7 @@ def test_network_gain_over_method(hqa):
     cfg10 = SG.SurrogateConfig(steps=S, frac=0.1)
     mlp10 = _train(hqa, SG, cfg10, R)
     g10 = SG.gated_run(test, mlp10, cfg10, R, seed=5)
-    mis10, _, acc10 = SG.judge(g10, full)
+    mis10, _, acc10 = SG.score_against_full(g10, full)
     print(f"10%: mislabel net {np.median(mis10):.3f}; accepted {acc10.sum()} of {R}; "
           f"median expected errors {g10['expected_errors'].median().item():.0f}")
     assert np.median(mis10) > 0.4
@@ -151,7 +151,7 @@ def test_network_gain_over_method(hqa):
     assert g10["md_steps"] == S * R
 
 
-def test_gate_accepts_and_is_judged(hqa):
+def test_gate_accepts_and_is_scored(hqa):
     """A loose threshold accepts replicas; their cut loss and mislabel rate come
     from the full run, and rejected replicas keep the full run's result bitwise."""
     from paper_2004_03972_gb300 import surrogate as SG
@@ -163,7 +163,7 @@ def test_gate_accepts_and_is_judged(hqa):
     cfg.max_expected_errors = float(probe["expected_errors"].median())
     g = SG.gated_run(test, mlp, cfg, R, seed=3)
     full = SG.method_run(test, SG.SurrogateConfig(steps=S), R, seed=3)
-    mis, loss, acc = SG.judge(g, full)
+    mis, loss, acc = SG.score_against_full(g, full)
     assert 0 < acc.sum() < R
     assert g["md_steps"] == cfg.steps_c * R + (S - cfg.steps_c) * int((~acc).sum())
     rej = torch.from_numpy(~acc).cuda()
