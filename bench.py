@@ -239,13 +239,18 @@ def run_ours(args):
         ("frozen", (R, N), torch.uint8), ("energy", (RR,), torch.int64),
         ("cut", (RR,), torch.int64), ("tally", (RR, 2), torch.int32))}
 
-    def pipeline(prec, seed):
-        ctx.run(S, R, seed=seed, sched=sched, precision=prec, out=out)
+    sub_out = (torch.empty((R, N), dtype=torch.int8, device=dev),
+               torch.empty((R,), dtype=torch.int64, device=dev))
+
+    def pipeline(prec, seed, st=None):
+        ctx.run(S, R, seed=seed, sched=sched, precision=prec, out=out, stream=st)
         if batch:
             return None   # the batch pipeline ends at readout + energy (no batched sub-solve)
-        return ctx.solve_sub(out["spins"], out["frozen"], n)
+        return ctx.solve_sub(out["spins"], out["frozen"], n, stream=st, out=sub_out)
 
     def timed(fn, K, W):
+        """CUDA-event times of K calls on the current stream, L2 flushed before each."""
+        st = torch.cuda.current_stream()
         for w in range(W):
             fn(w)
         torch.cuda.synchronize()
@@ -256,9 +261,9 @@ def run_ours(args):
             flush.fill_(float(k))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(st)
             fn(W + k)
-            e1.record(stream)
+            e1.record(st)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
         torch.cuda.synchronize()
@@ -271,6 +276,12 @@ def run_ours(args):
     with clocks:
         for name, prec_name in cfg["variants"]:
             prec = getattr(hqa, prec_name)
+            tuned = None
+            if cfg["kind"] != "dense":
+                # launch shape (kernel, replicas per block) by the library's autotuner
+                best, rows = ctx.autotune(R, precision=prec, probe_steps=64 if batch else min(S, 500))
+                tuned = {"kernel": best["kernel"], "replicas_per_block": best["replicas_per_block"],
+                         "candidates": [[k, rb, round(ms, 6)] for k, rb, ms in rows]}
             t_pipe = timed(lambda k, prec=prec: pipeline(prec, seed_base + k), args.steps, args.warmup)
             ctx.sync()
             # quality: MD readout cuts over the same seeds for every variant
@@ -283,7 +294,21 @@ def run_ours(args):
             md_out = {"phibar": out["phibar"]}   # MD kernel alone (roofline timing)
             t_md = timed(lambda k, prec=prec: ctx.run(S, R, seed=seed_base + k, sched=sched,
                                                       precision=prec, out=md_out), args.steps, 1)
+            t_graph = None
+            if cfg["kind"] != "dense":
+                # the same step as one CUDA-graph replay (fixed seed: the replay recomputes
+                # the whole run from the seeded initial state every time)
+                gs = torch.cuda.Stream(device=dev)
+                with torch.cuda.stream(gs):
+                    pipeline(prec, seed_base, gs)
+                    gs.synchronize()
+                    with hqa.capture(gs) as cap:
+                        pipeline(prec, seed_base, gs)
+                    t_graph = timed(lambda k: cap.graph.launch(gs), args.steps, args.warmup)
+                    cap.graph.close()
+                ctx.sync()
             variants[name] = dict(prec=prec, prec_name=prec_name, t_pipe=t_pipe, t_md=t_md,
+                                  t_graph=t_graph, tuned=tuned,
                                   cuts=allcuts, median_cut=float(np.median(allcuts)),
                                   cut_ci95_halfwidth=bootstrap_halfwidth(allcuts),
                                   mean_cut=float(np.mean(allcuts)))
@@ -341,9 +366,10 @@ def run_ours(args):
     clk = clocks.summary()
     hv = variants[head]
     if batch:
-        plan = {"kernel": hqa.KERNEL_SCALAR, "replicas_per_block": 0, "members": count,
-                "note": "persistent batch kernel, replica blocking chosen per batch"}
-        kname = f"k_sparse_md_batch<*,{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
+        rb = hv["tuned"]["replicas_per_block"]
+        plan = {"kernel": hqa.KERNEL_SCALAR, "replicas_per_block": rb, "members": count,
+                "note": "persistent batch kernel, replica blocking by the autotuner"}
+        kname = f"k_sparse_md_batch<{rb},{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
     else:
         plan = ctx.plan(R, precision=hv["prec"])
         kname = kernel_name(hqa, plan, hv["prec_name"])
@@ -388,6 +414,9 @@ def run_ours(args):
                    "n_ambivalent": n, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas only, {ws} GPU(s)"},
         "variants": {k: {"spin_updates_per_s": su_step * args.steps / sum(v["t_pipe"]),
+                         "graph_replay_spin_updates_per_s":
+                             su_step * args.steps / sum(v["t_graph"]) if v["t_graph"] else None,
+                         "autotuned": v["tuned"],
                          "md_kernel_ms": 1e3 * float(np.mean(v["t_md"])),
                          "median_cut": v["median_cut"], "cut_ci95_halfwidth": v["cut_ci95_halfwidth"],
                          "mean_cut": v["mean_cut"], "equal_cut_vs_plain": eq[k]}

@@ -402,7 +402,12 @@ hqa_status hqa_autotune(hqa_ctx* ctx, const hqa_schedule* sched, int32_t replica
  * graph.  hqa_capture_end must follow every successful hqa_capture_begin.
  * The graph replays the same launches with the same pointers and
  * arguments: the caller keeps those buffers alive and may change their
- * contents between replays.  hqa_sync is not capturable. */
+ * contents between replays.  The graph also reads device buffers and tables
+ * its contexts own (schedule table, workspaces, batch work tables): once a
+ * later call has reallocated or re-uploaded any of them (another step
+ * count, dt, seed of a batch run, a larger workspace), or a context is
+ * destroyed, hqa_graph_launch refuses the graph with HQA_ERR_INVALID_ARG.
+ * hqa_sync is not capturable. */
 typedef struct hqa_graph hqa_graph;
 hqa_status hqa_capture_begin(void* stream);
 hqa_status hqa_capture_end(void* stream, hqa_graph** out);

@@ -50,10 +50,24 @@ cudaError_t hqa_smem_attr(const void* kernel, size_t smem)
     return e;
 }
 
-hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes)
+namespace {
+// live contexts, so that a graph can tell a destroyed context from a live one
+std::mutex g_live_mu;
+std::map<const hqa_ctx*, uint64_t> g_live;   // context -> unique id (no reuse)
+uint64_t g_next_uid = 1;
+thread_local std::vector<hqa_ctx*> t_touched;
+}  // namespace
+
+void hqa_capture_touch(hqa_ctx* ctx)
+{
+    if (t_capturing && ctx) t_touched.push_back(ctx);
+}
+
+hqa_status hqa_reserve(hqa_ctx* ctx, void** p, size_t* cap, size_t bytes)
 {
     if (bytes <= *cap && *p) return HQA_OK;
     if (t_capturing) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
+    ++ctx->generation;
     if (*p) {
         cudaFree(*p);
         *p = nullptr;
@@ -149,6 +163,11 @@ hqa_status finish_create(hqa_ctx* c, hqa_ctx** out)
     }
     HQA_CUDA_TRY(cudaMalloc(&c->d_status, sizeof(uint32_t)));
     HQA_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+    {
+        std::lock_guard<std::mutex> lock(g_live_mu);
+        c->uid = g_next_uid++;
+        g_live[c] = c->uid;
+    }
     *out = c;
     return HQA_OK;
 }
@@ -225,6 +244,7 @@ hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t
         HQA_CUDA_TRY(cudaMalloc(&c->d_sched, bytes));
         c->sched_cap = bytes;
     }
+    ++c->generation;
     // synchronous copy: the device may still read the previous table
     HQA_CUDA_TRY(cudaDeviceSynchronize());
     HQA_CUDA_TRY(cudaMemcpy(c->d_sched, t.data(), bytes, cudaMemcpyHostToDevice));
@@ -325,7 +345,7 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     const bool tmp_spins = want_energy && !out->spins;
     size_t need = (tmp_phibar ? RN * sizeof(float) : 0) + (tmp_spins ? RN : 0);
     if (need) {
-        s = hqa_reserve(&ctx->d_ws, &ctx->ws_cap, need);
+        s = hqa_reserve(ctx, &ctx->d_ws, &ctx->ws_cap, need);
         if (s != HQA_OK) return s;
     }
     char* ws = static_cast<char*>(ctx->d_ws);
@@ -517,6 +537,11 @@ hqa_status hqa_create_batch(int32_t count, hqa_ctx* const* instances, hqa_ctx** 
     if (cudaMemcpy(c->d_binst, tab.data(), tab.size() * sizeof(BatchInst), cudaMemcpyHostToDevice) !=
         cudaSuccess)
         return fail(HQA_ERR_CUDA);
+    {
+        std::lock_guard<std::mutex> lock(g_live_mu);
+        c->uid = g_next_uid++;
+        g_live[c] = c->uid;
+    }
     *out = c;
     return HQA_OK;
 }
@@ -577,7 +602,7 @@ static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, i
     if (tmp_phibar) need += RN * sizeof(float);
     if (tmp_spins) need += RN;
     if (need) {
-        s = hqa_reserve(&ctx->d_ws, &ctx->ws_cap, need);
+        s = hqa_reserve(ctx, &ctx->d_ws, &ctx->ws_cap, need);
         if (s != HQA_OK) return s;
     }
     char* ws = static_cast<char*>(ctx->d_ws);
@@ -616,6 +641,7 @@ hqa_status hqa_run(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t s
                    int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
                    const hqa_result* out, void* stream)
 {
+    hqa_capture_touch(ctx);
     return hqa_capture_note(run_impl(ctx, sched, dt, steps, replicas, seed, opts, out, stream));
 }
 
@@ -647,6 +673,7 @@ static hqa_status local_field_impl(hqa_ctx* ctx, int32_t replicas, const float* 
 hqa_status hqa_local_field(hqa_ctx* ctx, int32_t replicas, const float* phi, float* L,
                            const hqa_run_opts* opts, void* stream)
 {
+    hqa_capture_touch(ctx);
     return hqa_capture_note(local_field_impl(ctx, replicas, phi, L, opts, stream));
 }
 
@@ -665,6 +692,7 @@ static hqa_status readout_impl(hqa_ctx* ctx, int32_t replicas, const float* phib
 hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int32_t n,
                        int8_t* spins, uint8_t* frozen, int32_t* tally, void* stream)
 {
+    hqa_capture_touch(ctx);
     return hqa_capture_note(readout_impl(ctx, replicas, phibar, n, spins, frozen, tally, stream));
 }
 
@@ -682,6 +710,7 @@ static hqa_status energy_impl(hqa_ctx* ctx, int32_t replicas, const int8_t* spin
 hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
                       int64_t* cut, void* stream)
 {
+    hqa_capture_touch(ctx);
     return hqa_capture_note(energy_impl(ctx, replicas, spins, energy, cut, stream));
 }
 
@@ -700,6 +729,7 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
                          const uint8_t* frozen, int32_t n, int8_t* out_spins,
                          int64_t* out_energy, void* stream)
 {
+    hqa_capture_touch(ctx);
     return hqa_capture_note(solve_sub_impl(ctx, replicas, spins, frozen, n, out_spins, out_energy, stream));
 }
 
@@ -788,6 +818,7 @@ hqa_status hqa_capture_begin(void* stream)
                                         cudaStreamCaptureModeThreadLocal));
     t_capturing = true;
     t_capture_status = HQA_OK;
+    t_touched.clear();
     return HQA_OK;
 }
 
@@ -803,6 +834,7 @@ hqa_status hqa_capture_end(void* stream, hqa_graph** out)
     if (e != cudaSuccess || first != HQA_OK || !g) {
         (void)cudaGetLastError();
         if (g) cudaGraphDestroy(g);
+        t_touched.clear();
         return first != HQA_OK ? first : HQA_ERR_CUDA;
     }
     cudaGraphExec_t x = nullptr;
@@ -810,6 +842,7 @@ hqa_status hqa_capture_end(void* stream, hqa_graph** out)
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         cudaGraphDestroy(g);
+        t_touched.clear();
         return HQA_ERR_CUDA;
     }
     hqa_graph* h = new (std::nothrow) hqa_graph;
@@ -820,13 +853,29 @@ hqa_status hqa_capture_end(void* stream, hqa_graph** out)
     }
     h->graph = g;
     h->exec = x;
+    for (hqa_ctx* c : t_touched) {
+        bool seen = false;
+        for (const auto& d : h->deps) seen = seen || d.ctx == c;
+        if (!seen) h->deps.push_back({c, c->uid, c->generation});
+    }
+    t_touched.clear();
     *out = h;
     return HQA_OK;
 }
 
 hqa_status hqa_graph_launch(hqa_graph* g, void* stream)
 {
-    if (!g) return HQA_ERR_INVALID_ARG;
+    if (!g || t_capturing) return HQA_ERR_INVALID_ARG;
+    {
+        // every context the graph uses must be alive, with the buffers and tables
+        // it had at capture (a reallocation would leave the graph a dangling pointer)
+        std::lock_guard<std::mutex> lock(g_live_mu);
+        for (const auto& d : g->deps) {
+            const auto it = g_live.find(d.ctx);
+            if (it == g_live.end() || it->second != d.uid || d.ctx->generation != d.generation)
+                return HQA_ERR_INVALID_ARG;
+        }
+    }
     HQA_CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
     return HQA_OK;
 }
@@ -842,6 +891,10 @@ void hqa_graph_destroy(hqa_graph* g)
 void hqa_destroy(hqa_ctx* ctx)
 {
     if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> lock(g_live_mu);
+        g_live.erase(ctx);
+    }
     cudaDeviceSynchronize();
     free_ctx_device(ctx);
     delete ctx;

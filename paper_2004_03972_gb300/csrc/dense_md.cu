@@ -225,7 +225,7 @@ hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, 
     const int Kpad = ctx->Mpad;
     const int Rpad = (R + kFieldBN - 1) / kFieldBN * kFieldBN;
     const size_t bytes = (size_t)Rpad * Kpad * sizeof(__nv_bfloat16);
-    hqa_status s = hqa_reserve(&ctx->d_ws, &ctx->ws_cap, bytes);
+    hqa_status s = hqa_reserve(ctx, &ctx->d_ws, &ctx->ws_cap, bytes);
     if (s != HQA_OK) return s;
     __nv_bfloat16* phib = static_cast<__nv_bfloat16*>(ctx->d_ws);
     k_phi_to_bf16<<<std::min<size_t>(4096, (bytes / 2 + 255) / 256), 256, 0, st>>>(phi, R, ctx->N, Rpad,
@@ -640,7 +640,7 @@ hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S,
     // state: phi, p, w (FP32), two BF16 operand buffers, 2 Nc counters
     const size_t off_p = n * 4, off_w = 2 * n * 4, off_b = 3 * n * 4, off_g = off_b + 2 * nb * 2;
     const size_t need = off_g + (size_t)2 * Nc * sizeof(unsigned int);
-    hqa_status s = hqa_reserve(&ctx->d_state, &ctx->state_cap, need);
+    hqa_status s = hqa_reserve(ctx, &ctx->d_state, &ctx->state_cap, need);
     if (s != HQA_OK) return s;
     char* b = static_cast<char*>(ctx->d_state);
     DenseMDArgs a{};

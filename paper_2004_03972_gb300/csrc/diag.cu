@@ -63,8 +63,9 @@ extern "C" hqa_status hqa_hmd(hqa_ctx* ctx, const hqa_schedule* sched, double ta
     if (sched->kind != HQA_SCHED_PAPER && sched->kind != HQA_SCHED_LINEAR_GAMMA)
         return HQA_ERR_INVALID_ARG;
     if (sched->M < 2 || sched->M > 16 || !std::isfinite(sched->hstep)) return HQA_ERR_INVALID_ARG;
+    hqa_capture_touch(ctx);
     const size_t RN = (size_t)replicas * ctx->N;
-    hqa_status s = hqa_reserve(&ctx->d_diag, &ctx->diag_cap, RN * sizeof(float));
+    hqa_status s = hqa_reserve(ctx, &ctx->d_diag, &ctx->diag_cap, RN * sizeof(float));
     if (s != HQA_OK) return s;
     float* L = static_cast<float*>(ctx->d_diag);
     s = hqa_local_field(ctx, replicas, phi, L, opts, stream);

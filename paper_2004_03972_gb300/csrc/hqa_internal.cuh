@@ -82,6 +82,12 @@ struct BatchInst {
 struct hqa_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    struct Dep {
+        hqa_ctx* ctx;
+        uint64_t uid;          // the context's unique id (addresses can be reused)
+        uint64_t generation;   // its generation at capture
+    };
+    std::vector<Dep> deps;
 };
 
 struct hqa_ctx {
@@ -145,6 +151,10 @@ struct hqa_ctx {
     void* d_bwork = nullptr;        // per-run instance arguments, work items, queue counter
     size_t bwork_cap = 0;
     std::vector<char> bwork_host;   // what d_bwork holds (tables are uploaded only on change)
+    // bumped whenever a device buffer of the context is reallocated or a device
+    // table (schedule, batch work tables) is re-uploaded: captured graphs check it
+    uint64_t generation = 0;
+    uint64_t uid = 0;               // unique per created context
 
     // dense contexts whose couplings are exact in BF16: tensor-core operand
     bool dense_tc = false;
@@ -156,13 +166,16 @@ struct hqa_ctx {
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;
 // cudaFree synchronises the device, so in-flight users are finished).
 // During a capture a needed reallocation fails with HQA_ERR_UNSUPPORTED.
-hqa_status hqa_reserve(void** p, size_t* cap, size_t bytes);
+hqa_status hqa_reserve(hqa_ctx* ctx, void** p, size_t* cap, size_t bytes);
 
 // Stream capture (hqa_capture_begin/end) of the calling thread: while it is
 // open, anything that would allocate, upload from the host or synchronise
 // returns HQA_ERR_UNSUPPORTED, and the first failure of a capturing call is
 // kept for hqa_capture_end.
 bool hqa_capturing();
+// Records that the capture uses `ctx`'s device buffers: the graph refuses to
+// replay once the context has reallocated or re-uploaded any of them.
+void hqa_capture_touch(hqa_ctx* ctx);
 double hqa_sched_alpha(const hqa_schedule* s, double tau);
 double hqa_sched_beta(const hqa_schedule* s, double tau);
 hqa_status hqa_capture_note(hqa_status s);

@@ -590,7 +590,7 @@ hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* pl, const StepCo
         a.gstate = nullptr;
     } else {
         const int blocks = (R + RB - 1) / RB;
-        hqa_status s = hqa_reserve(&ctx->d_state, &ctx->state_cap, (size_t)blocks * sb);
+        hqa_status s = hqa_reserve(ctx, &ctx->d_state, &ctx->state_cap, (size_t)blocks * sb);
         if (s != HQA_OK) return s;
         a.state_in_smem = 0;
         a.gstate = static_cast<float*>(ctx->d_state);
@@ -709,11 +709,11 @@ hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_s
     const size_t off_items = (args.size() * sizeof(MDArgs) + 255) & ~(size_t)255;
     const size_t off_cnt = off_items + ((sorted.size() * sizeof(BatchItem) + 255) & ~(size_t)255);
     void* const held = b->d_bwork;
-    hqa_status s = hqa_reserve(&b->d_bwork, &b->bwork_cap, off_cnt + 256);
+    hqa_status s = hqa_reserve(b, &b->d_bwork, &b->bwork_cap, off_cnt + 256);
     if (s != HQA_OK) return s;
     if (b->d_bwork != held) b->bwork_host.clear();
     if (gslot) {
-        s = hqa_reserve(&b->d_state, &b->state_cap, (size_t)grid * gslot);
+        s = hqa_reserve(b, &b->d_state, &b->state_cap, (size_t)grid * gslot);
         if (s != HQA_OK) return s;
         for (auto& a : args)
             if (!a.state_in_smem) {
@@ -731,6 +731,7 @@ hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_s
     std::copy(ib, ib + sorted.size() * sizeof(BatchItem), tab.begin() + (std::ptrdiff_t)off_items);
     if (tab != b->bwork_host) {
         if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
+        ++b->generation;
         b->bwork_host.clear();
         // pageable source: the copy is staged before cudaMemcpyAsync returns
         HQA_CUDA_TRY(cudaMemcpyAsync(w, tab.data(), tab.size(), cudaMemcpyHostToDevice, st));

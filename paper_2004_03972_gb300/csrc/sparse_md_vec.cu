@@ -876,7 +876,7 @@ hqa_status hqa_vec_launch_md(hqa_ctx* ctx, const SparsePlan* pl, const StepCoef*
     const size_t smem = hqa_vec_smem_bytes(ctx, pl->RB, pl->prec, pl->ent_bytes);
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     const int blocks = (R + pl->RB - 1) / pl->RB;
-    hqa_status s = hqa_reserve(&ctx->d_state, &ctx->state_cap,
+    hqa_status s = hqa_reserve(ctx, &ctx->d_state, &ctx->state_cap,
                                (size_t)blocks * pl->Npad * pl->RB * sizeof(float));
     if (s != HQA_OK) return s;
     VArgs a = common_args(ctx, pl, R);

@@ -247,7 +247,7 @@ hqa_status hqa_launch_subsolve(hqa_ctx* ctx, int32_t R, const int8_t* spins,
     // keys (64-bit atomics) start on a 256-byte boundary after the prep records
     const size_t keys_off = ((size_t)R * sizeof(SubPrep) + 255) & ~(size_t)255;
     const size_t need = keys_off + (size_t)R * sizeof(unsigned long long);
-    hqa_status s = hqa_reserve(&ctx->d_sub, &ctx->sub_cap, need);
+    hqa_status s = hqa_reserve(ctx, &ctx->d_sub, &ctx->sub_cap, need);
     if (s != HQA_OK) return s;
     SubPrep* prep = static_cast<SubPrep*>(ctx->d_sub);
     unsigned long long* keys =
@@ -336,6 +336,7 @@ extern "C" hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, cons
         return HQA_ERR_CUDA;
     }
     if (dev != ctx->device) return HQA_ERR_INVALID_ARG;  // the scratch address is per device
+    hqa_capture_touch(ctx);
     unsigned char* base = nullptr;
     hqa_status s = sub_scratch_address(dev, &base);
     if (s != HQA_OK) return s;

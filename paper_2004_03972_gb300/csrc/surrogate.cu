@@ -154,11 +154,12 @@ hqa_status hqa_run_features(hqa_ctx* ctx, const hqa_schedule* sched, double dt, 
     if (opts) o = *opts;
     else hqa_run_opts_default(&o);
     if (o.start_step != 0) return HQA_ERR_INVALID_ARG;
+    hqa_capture_touch(ctx);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t RN = (size_t)replicas * ctx->N;
     // workspace: accumulators (float4), phibar, L
     const size_t need = RN * (16 + 4 + 4);
-    hqa_status s = hqa_reserve(&ctx->d_feat, &ctx->feat_cap, need);
+    hqa_status s = hqa_reserve(ctx, &ctx->d_feat, &ctx->feat_cap, need);
     if (s != HQA_OK) return s;
     float4* acc = static_cast<float4*>(ctx->d_feat);
     float* phibar = reinterpret_cast<float*>(acc + RN);
@@ -196,9 +197,10 @@ hqa_status hqa_surrogate_readout(hqa_ctx* ctx, int32_t replicas, const float* lo
                                  uint8_t* accept, float* expected_errors, void* stream)
 {
     if (!ctx || ctx->is_batch || replicas < 1 || !logits || !spins || !frozen) return HQA_ERR_INVALID_ARG;
+    hqa_capture_touch(ctx);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t RN = (size_t)replicas * ctx->N;
-    hqa_status s = hqa_reserve(&ctx->d_feat, &ctx->feat_cap, RN * 4);
+    hqa_status s = hqa_reserve(ctx, &ctx->d_feat, &ctx->feat_cap, RN * 4);
     if (s != HQA_OK) return s;
     float* key = static_cast<float*>(ctx->d_feat);
     k_sur_key<<<grid_for(RN), 256, 0, st>>>(RN, logits, key);

@@ -64,7 +64,7 @@ extern "C" hqa_status hqa_autotune(hqa_ctx* ctx, const hqa_schedule* sched, int3
     // spin-indexed outputs: [R][N], or the members' [R][N_k] blocks of a batch
     const size_t spins = ctx->is_batch ? (size_t)ctx->total_spins : (size_t)ctx->N;
     const size_t RN = (size_t)replicas * spins;
-    hqa_status s = hqa_reserve(&ctx->d_tune, &ctx->tune_cap, 2 * RN * sizeof(float));
+    hqa_status s = hqa_reserve(ctx, &ctx->d_tune, &ctx->tune_cap, 2 * RN * sizeof(float));
     if (s != HQA_OK) return s;
     hqa_result res{};
     res.phi = static_cast<float*>(ctx->d_tune);

@@ -163,3 +163,30 @@ def test_autotune_batch_and_errors(hqa):
     assert torch.equal(x["phi"], y["phi"]) and torch.equal(x["cut"], y["cut"])
     with pytest.raises(hqa.HQAError):
         b.autotune(R, probe_steps=0)
+
+
+def test_stale_graph_is_refused(hqa):
+    """A graph whose context re-uploaded its schedule table (another step count) or
+    was destroyed is refused instead of replaying dangling device pointers."""
+    inst = instances.torus_pm1(16, 16, 4)
+    ctx = hqa.Context.from_instance(inst)
+    R = 8
+    st = torch.cuda.Stream()
+    out = _outs(R, inst.N, R)
+    ctx.run(300, R, out=out, stream=st)
+    with hqa.capture(st) as cap:
+        ctx.run(300, R, out=out, stream=st)
+    cap.graph.launch(st)
+    st.synchronize()
+    ctx.run(100, R, out=out, stream=st)            # new schedule table
+    with pytest.raises(hqa.HQAError) as ei:
+        cap.graph.launch(st)
+    assert ei.value.status == 1
+    ctx.run(300, R, out=out, stream=st)
+    with hqa.capture(st) as cap2:
+        ctx.run(300, R, out=out, stream=st)
+    cap2.graph.launch(st)
+    st.synchronize()
+    ctx.close()
+    with pytest.raises(hqa.HQAError):
+        cap2.graph.launch(st)
