@@ -278,7 +278,7 @@ hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, const int8_t* s
  * coupling entry (padding), shared-memory wavefronts per conflict-free
  * wavefront (bank conflicts), and mean/max warp load (balance). */
 typedef struct {
-    int32_t kernel;              /* HQA_KERNEL_SCALAR or HQA_KERNEL_VECTOR */
+    int32_t kernel;              /* HQA_KERNEL_SCALAR, _VECTOR or _DENSE */
     int32_t replicas_per_block;
     int32_t blocks;              /* CTAs per launch */
     int32_t threads;             /* threads per CTA */
@@ -286,6 +286,8 @@ typedef struct {
     double pad_ratio;
     double conflict_ratio;
     double balance;
+    int32_t chunks;              /* sequential launches over replica chunks (dense: each
+                                    chunk's per-step data fits in L2), else 1 */
 } hqa_plan_info;
 
 hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* opts,

@@ -113,6 +113,9 @@ hqa_status finish_create(hqa_ctx* c, hqa_ctx** out)
     int optin = 0;
     HQA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     c->smem_optin = (size_t)optin;
+    int l2 = 0;
+    HQA_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device));
+    c->l2_bytes = (size_t)l2;
     const int N = c->N;
     c->nnz = (int64_t)c->col.size();
     if (c->nnz >= (int64_t)1 << 31) return HQA_ERR_TOO_LARGE;
@@ -509,6 +512,7 @@ hqa_status hqa_create_batch(int32_t count, hqa_ctx* const* instances, hqa_ctx** 
     c->device = instances[0]->device;
     c->sm_count = instances[0]->sm_count;
     c->smem_optin = instances[0]->smem_optin;
+    c->l2_bytes = instances[0]->l2_bytes;
     c->integer = true;
     c->unit = true;
     std::vector<BatchInst> tab(count);
@@ -747,14 +751,17 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
     if (o.kernel == HQA_KERNEL_DENSE ||
         (o.kernel == HQA_KERNEL_AUTO && tc_prec && hqa_dense_md_possible(ctx, replicas))) {
         int nh = 0, grid = 0;
-        if (!ctx->dense_tc || !tc_prec || !hqa_dense_md_geometry(ctx, replicas, &nh, &grid))
-            return HQA_ERR_UNSUPPORTED;
+        if (!ctx->dense_tc || !tc_prec) return HQA_ERR_UNSUPPORTED;
+        const int C = hqa_dense_md_chunks(ctx, replicas, o.precision == HQA_PREC_BF16X2);
+        const int Rc = (replicas + C - 1) / C;
+        if (!hqa_dense_md_geometry(ctx, Rc, &nh, &grid)) return HQA_ERR_UNSUPPORTED;
         out->kernel = HQA_KERNEL_DENSE;
         out->replicas_per_block = 2 * nh;
         out->blocks = grid;
         out->threads = 320;
         out->smem_bytes = 0;
-        out->pad_ratio = (double)grid * 128 * 2 * nh / ((double)ctx->N * replicas);
+        out->chunks = C;
+        out->pad_ratio = (double)C * grid * 128 * 2 * nh / ((double)ctx->N * replicas);
         out->conflict_ratio = 1.0;
         out->balance = 1.0;
         return HQA_OK;
@@ -764,6 +771,7 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
     s = choose_plan(ctx, replicas, o, &plan);
     if (s != HQA_OK) return s;
     out->kernel = plan->vec ? HQA_KERNEL_VECTOR : HQA_KERNEL_SCALAR;
+    out->chunks = 1;
     out->replicas_per_block = plan->RB;
     out->blocks = (replicas + plan->RB - 1) / plan->RB;
     if (plan->vec) {

@@ -282,6 +282,7 @@ struct DenseMDArgs {
     uint32_t* status;
     int64_t S;
     int W, N, Npad, Rpad, R, KT, Mt, M;
+    int rep0;                // global index of this launch's first replica (random draws)
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
@@ -505,7 +506,7 @@ __global__ void k_dense_init(DenseMDArgs a, uint64_t seed, int init, const float
         const int r = (int)(idx / a.Npad), i = (int)(idx % a.Npad);
         float phi = 0.f, p = 0.f;
         if (r < a.R && i < a.N) {
-            const uint64_t c = ((uint64_t)r << 32) | (uint64_t)i;
+            const uint64_t c = ((uint64_t)(a.rep0 + r) << 32) | (uint64_t)i;
             if (init == HQA_INIT_GIVEN) {
                 phi = phi0[(size_t)r * a.N + i];
                 p = p0[(size_t)r * a.N + i];
@@ -609,9 +610,50 @@ static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid
 
 bool hqa_dense_md_possible(const hqa_ctx* ctx, int32_t R)
 {
-    if (!ctx->dense_tc) return false;
-    return pick_nh(ctx->Mpad / BM, R, ctx->sm_count) > 0;
+    if (!ctx->dense_tc || R < 1) return false;
+    return pick_nh(ctx->Mpad / BM, 1, ctx->sm_count) > 0;   // larger R runs in chunks
 }
+
+namespace {
+
+// Bytes one step touches for R replicas: FP32 phi and p, the two BF16 operand
+// buffers (doubled for the split operand) and the coupling operand.
+size_t dense_step_bytes(const hqa_ctx* ctx, int32_t R, bool split)
+{
+    int NH = 0, grid = 0;
+    if (!hqa_dense_md_geometry(ctx, R, &NH, &grid)) return SIZE_MAX;
+    const size_t Rpad = (size_t)(grid / (ctx->Mpad / BM)) * 2 * NH;
+    const size_t n = Rpad * (size_t)ctx->Mpad;
+    const size_t J = (size_t)ctx->Mpad * ctx->Mpad * 2 * (split ? 2 : 1);
+    return n * (8 + (split ? 8 : 4)) + J;
+}
+
+// Replica chunks run one after another, each a full trajectory.  A CTA's step
+// costs its MMA columns (NH per half, doubled for the split operand) plus a
+// fixed part worth ~150 columns (streaming its 128-row coupling tile through
+// shared memory, the column-group barrier, pipeline fill), measured on K2000;
+// a chunk whose step touches more than ~70% of L2 streams its state from HBM
+// every step, which about doubles the step.  C minimises the sum over chunks.
+int dense_chunks(const hqa_ctx* ctx, int32_t R, bool split)
+{
+    const double budget = 0.7 * (double)(ctx->l2_bytes ? ctx->l2_bytes : (size_t)96 << 20);
+    int best = 1;
+    double best_t = 1e300;
+    for (int C = 1; C <= 16 && C <= R; ++C) {
+        const int Rc = (R + C - 1) / C;
+        int NH = 0, grid = 0;
+        if (!hqa_dense_md_geometry(ctx, Rc, &NH, &grid)) continue;
+        const double spill = (double)dense_step_bytes(ctx, Rc, split) > budget ? 2.0 : 1.0;
+        const double t = (double)C * ((split ? 2.0 : 1.0) * NH + 150.0) * spill;
+        if (t < best_t - 1e-9) {
+            best_t = t;
+            best = C;
+        }
+    }
+    return best;
+}
+
+}  // namespace
 
 int hqa_dense_md_geometry(const hqa_ctx* ctx, int32_t R, int* nh, int* grid)
 {
@@ -624,10 +666,10 @@ int hqa_dense_md_geometry(const hqa_ctx* ctx, int32_t R, int* nh, int* grid)
     return 1;
 }
 
-hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
-                               int32_t R, uint64_t seed, int init, const float* phi0,
-                               const float* p0, int M, float* phi_out, float* p_out,
-                               float* phibar_out, bool split, cudaStream_t st)
+static hqa_status dense_md_chunk(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
+                                 int32_t R, int32_t rep0, uint64_t seed, int init,
+                                 const float* phi0, const float* p0, int M, float* phi_out,
+                                 float* p_out, float* phibar_out, bool split, cudaStream_t st)
 {
     int NH = 0, grid = 0;
     if (!hqa_dense_md_geometry(ctx, R, &NH, &grid)) return HQA_ERR_TOO_LARGE;
@@ -661,6 +703,7 @@ hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S,
     a.KT = Npad / BK;
     a.Mt = Mt;
     a.M = M;
+    a.rep0 = rep0;
     CUtensorMap tmB;
     if (!make_tmap_bf16(&tmB, a.phib, (uint64_t)2 * Rpad, split ? 2 * Npad : Npad, NH))
         return HQA_ERR_CUDA;
@@ -692,4 +735,29 @@ hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S,
     k_dense_out<<<std::min<size_t>(8192, ((size_t)R * ctx->N + 255) / 256), 256, 0, st>>>(
         a, 1.0f / (float)nwin, phi_out, p_out, phibar_out);
     return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
+
+int hqa_dense_md_chunks(const hqa_ctx* ctx, int32_t R, bool split)
+{
+    return dense_chunks(ctx, R, split);
+}
+
+hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
+                               int32_t R, uint64_t seed, int init, const float* phi0,
+                               const float* p0, int M, float* phi_out, float* p_out,
+                               float* phibar_out, bool split, cudaStream_t st)
+{
+    const int C = dense_chunks(ctx, R, split);
+    const int Rc = (R + C - 1) / C;
+    const size_t N = (size_t)ctx->N;
+    for (int r0 = 0; r0 < R; r0 += Rc) {
+        const int Rk = std::min(Rc, R - r0);
+        const size_t o = (size_t)r0 * N;
+        hqa_status s = dense_md_chunk(ctx, d_sched, S, W, Rk, r0, seed, init,
+                                      phi0 ? phi0 + o : nullptr, p0 ? p0 + o : nullptr, M,
+                                      phi_out ? phi_out + o : nullptr, p_out ? p_out + o : nullptr,
+                                      phibar_out ? phibar_out + o : nullptr, split, st);
+        if (s != HQA_OK) return s;
+    }
+    return HQA_OK;
 }

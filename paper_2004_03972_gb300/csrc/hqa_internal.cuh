@@ -58,6 +58,7 @@ struct SparsePlan {
     int* d_warp_off = nullptr;    // [NW + 1] offsets into d_tuple_list
     int* d_tuple_list = nullptr;  // tuples in per-warp order
     double balance = 0.0;         // mean warp load / max warp load
+    int max_wt = 0;               // most tuples any warp owns (register-resident state if <= 4)
 };
 
 // Orders one section of G neighbour lists into K positions so that rows read
@@ -94,6 +95,7 @@ struct hqa_ctx {
     int device = 0;
     int sm_count = 0;
     size_t smem_optin = 0;
+    size_t l2_bytes = 0;
     int32_t N = 0;
     int64_t nnz = 0;            // stored off-diagonal entries (both triangles)
     bool dense_input = false;
@@ -214,6 +216,7 @@ hqa_status hqa_dense_setup(hqa_ctx* ctx, const float* J);
 hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, cudaStream_t st);
 bool hqa_dense_md_possible(const hqa_ctx* ctx, int32_t R);
 int hqa_dense_md_geometry(const hqa_ctx* ctx, int32_t R, int* nh, int* grid);
+int hqa_dense_md_chunks(const hqa_ctx* ctx, int32_t R, bool split);
 hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
                                int32_t R, uint64_t seed, int init, const float* phi0,
                                const float* p0, int M, float* phi_out, float* p_out,

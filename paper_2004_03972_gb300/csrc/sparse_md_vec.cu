@@ -20,7 +20,12 @@
 //   * sums use Blackwell's packed FP32 add (add.rn.f32x2);
 //   * tuples are assigned to warps on the host (longest-processing-time
 //     first); one __syncthreads() per leapfrog step; window sums live in
-//     global memory (touched only in the last W steps).
+//     global memory (touched only in the last W steps);
+//   * a lane updates the same rows at every step (the tuple-to-warp map is
+//     fixed for the launch), so when no warp owns more than four tuples
+//     the FP32 flux and momentum of the lane's rows stay in its
+//     registers for the whole trajectory: the kick reads no shared memory
+//     and writes only the next operand buffer.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,6 +38,14 @@
 namespace {
 
 constexpr int kMaxThreads = 1024;
+// Register-resident state: a warp owning at most `reg` tuples (1, 2 or 4) keeps
+// its rows' flux and momentum in registers; the launch bound then allows
+// reg_threads(reg, bf16) threads, chosen so that no variant spills
+// (1024 / 896 threads -> 64 / 72 registers, 832 / 704 -> 72 / 88, 512 -> 128).
+__host__ __device__ constexpr int reg_threads(int reg, bool bf16)
+{
+    return reg == 1 ? (bf16 ? 896 : 1024) : reg == 2 ? (bf16 ? 704 : 832) : 512;
+}
 
 __device__ __forceinline__ uint64_t smix(uint64_t seed, uint64_t counter)
 {
@@ -198,6 +211,7 @@ struct VArgs {
     int64_t S;
     int32_t W, N, Npad, T, R, M, init;
     uint32_t ent_bytes;
+    int32_t reg;            // 0, or state in registers: every warp owns <= reg tuples
 };
 
 // Shared-memory layout (bytes):
@@ -205,8 +219,9 @@ struct VArgs {
 //   op[2]  : 2 step buffers, each [+ slots | - slots], Npad * RB * ES per half
 //   master : Npad * RB FP32 (BF16 operand only)
 //   p      : Npad * RB FP32
-template <int RB, bool BF16>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md_vec(const VArgs a)
+template <int RB, bool BF16, int REG>
+__global__ void __launch_bounds__(REG > 0 ? reg_threads(REG, BF16) : kMaxThreads, 1)
+    k_sparse_md_vec(const VArgs a)
 {
     constexpr int ES = BF16 ? 2 : 4;
     constexpr int V = 16 / ES;     // replicas per lane
@@ -266,6 +281,126 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_sparse_md_vec(const VArgs a)
     const int wbeg = __ldg(a.warp_off + warp), wend = __ldg(a.warp_off + warp + 1);
     const int64_t win0 = a.S - (int64_t)a.W;
     const int mhalf = (a.M - 2) / 2;
+    if constexpr (REG > 0) {
+        // this lane's rows: flux and momentum in registers for the whole trajectory
+        constexpr int RS = REG > 0 ? REG : 1;
+        float rphi[RS][V], rp[RS][V];
+        uint32_t rent[RS], re0[RS];
+        int rnh[RS];
+        float rhr[RS];
+        bool rok[RS];
+#pragma unroll
+        for (int kk = 0; kk < RS; ++kk) {
+            const int k = wbeg + kk;
+            rok[kk] = false;
+            rent[kk] = 0u;
+            rnh[kk] = 0;
+            re0[kk] = 0u;
+            rhr[kk] = 0.f;
+            if (k < wend) {
+                const int t = __ldg(a.tuple_list + k);
+                const int4 tp = __ldg(a.tuples + t);
+                rent[kk] = s0 + ((uint32_t)tp.x * G + g) * 16u;
+                rnh[kk] = tp.y;
+                const int row = __ldg(a.tuple_rows + t * G + g);
+                if (row >= 0) {
+                    rok[kk] = true;
+                    re0[kk] = (uint32_t)(__ldg(a.slot_of_row + row) * RB + q * V);
+                    rhr[kk] = a.h ? 2.f * __ldg(a.h + row) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int k4 = 0; k4 < V / 4; ++k4) {
+                uint4 x = make_uint4(0, 0, 0, 0), y = make_uint4(0, 0, 0, 0);
+                if (rok[kk]) {
+                    x = lds128((BF16 ? master : op0) + (re0[kk] + 4 * k4) * 4u);
+                    y = lds128(ps + (re0[kk] + 4 * k4) * 4u);
+                }
+                rphi[kk][4 * k4] = __uint_as_float(x.x); rphi[kk][4 * k4 + 1] = __uint_as_float(x.y);
+                rphi[kk][4 * k4 + 2] = __uint_as_float(x.z); rphi[kk][4 * k4 + 3] = __uint_as_float(x.w);
+                rp[kk][4 * k4] = __uint_as_float(y.x); rp[kk][4 * k4 + 1] = __uint_as_float(y.y);
+                rp[kk][4 * k4 + 2] = __uint_as_float(y.z); rp[kk][4 * k4 + 3] = __uint_as_float(y.w);
+            }
+        }
+        const int nk = wend - wbeg;
+        for (int64_t j = 0; j < a.S; ++j) {
+            const float4 cf = __ldg(reinterpret_cast<const float4*>(a.sched) + j);
+            const uint32_t cur = op0 + (uint32_t)(j & 1) * buf_bytes;
+            const uint32_t nxt = op0 + (uint32_t)((j & 1) ^ 1) * buf_bytes;
+            const bool in_win = j >= win0;
+#pragma unroll
+            for (int kk = 0; kk < RS; ++kk) {
+                if (kk >= nk) break;
+                float Lsum[V];
+                if constexpr (BF16) {
+                    tuple_field_bf16<G>(rent[kk], rnh[kk], cur + (uint32_t)q * 16u, Lsum);
+                } else {
+                    uint64_t acc[NP];
+                    tuple_field_vec<G, BF16>(rent[kk], rnh[kk], cur + (uint32_t)q * 16u, acc);
+#pragma unroll
+                    for (int u = 0; u < V; ++u) Lsum[u] = (u & 1) ? hi_f(acc[u >> 1]) : lo_f(acc[u >> 1]);
+                }
+                if (!rok[kk]) continue;
+#pragma unroll
+                for (int u = 0; u < V; ++u) {
+                    const float L = Lsum[u] + rhr[kk] * fabsf(rphi[kk][u]);
+                    const float phi2 = rphi[kk][u] * rphi[kk][u];
+                    float pw = rphi[kk][u];
+                    for (int m = 0; m < mhalf; ++m) pw *= phi2;
+                    rp[kk][u] = rp[kk][u] - fmaf(cf.x, pw, cf.y * L);
+                    rphi[kk][u] = fmaf(cf.z, rp[kk][u], rphi[kk][u]);
+                }
+                if constexpr (BF16) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) {
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(rphi[kk][2 * k2], rphi[kk][2 * k2 + 1]);
+                        pk[k2] = *reinterpret_cast<uint32_t*>(&b2);
+                    }
+                    sts128(nxt + re0[kk] * 2u, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+                    sts128(nxt + half_bytes + re0[kk] * 2u,
+                           make_uint4(pk[0] ^ 0x80008000u, pk[1] ^ 0x80008000u, pk[2] ^ 0x80008000u,
+                                      pk[3] ^ 0x80008000u));
+                } else {
+                    const uint4 f = make_uint4(__float_as_uint(rphi[kk][0]), __float_as_uint(rphi[kk][1]),
+                                               __float_as_uint(rphi[kk][2]), __float_as_uint(rphi[kk][3]));
+                    sts128(nxt + re0[kk] * 4u, f);
+                    sts128(nxt + half_bytes + re0[kk] * 4u,
+                           make_uint4(f.x ^ 0x80000000u, f.y ^ 0x80000000u, f.z ^ 0x80000000u,
+                                      f.w ^ 0x80000000u));
+                }
+                if (in_win) {
+#pragma unroll
+                    for (int k4 = 0; k4 < V / 4; ++k4) {
+                        float4* wp = reinterpret_cast<float4*>(gw + re0[kk] + 4 * k4);
+                        float4 w = *wp;
+                        w.x += rphi[kk][4 * k4]; w.y += rphi[kk][4 * k4 + 1];
+                        w.z += rphi[kk][4 * k4 + 2]; w.w += rphi[kk][4 * k4 + 3];
+                        *wp = w;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // final state back to the shared layout the output code reads
+        const uint32_t fin = op0 + (uint32_t)(a.S & 1) * buf_bytes;
+#pragma unroll
+        for (int kk = 0; kk < RS; ++kk) {
+            if (!rok[kk]) continue;
+#pragma unroll
+            for (int k4 = 0; k4 < V / 4; ++k4) {
+                const uint32_t o = (re0[kk] + 4 * k4) * 4u;
+                sts128(ps + o, make_uint4(__float_as_uint(rp[kk][4 * k4]), __float_as_uint(rp[kk][4 * k4 + 1]),
+                                          __float_as_uint(rp[kk][4 * k4 + 2]),
+                                          __float_as_uint(rp[kk][4 * k4 + 3])));
+                sts128((BF16 ? master : fin) + o,
+                       make_uint4(__float_as_uint(rphi[kk][4 * k4]), __float_as_uint(rphi[kk][4 * k4 + 1]),
+                                  __float_as_uint(rphi[kk][4 * k4 + 2]),
+                                  __float_as_uint(rphi[kk][4 * k4 + 3])));
+            }
+        }
+        __syncthreads();
+    } else
     for (int64_t j = 0; j < a.S; ++j) {
         const float4 cf = __ldg(reinterpret_cast<const float4*>(a.sched) + j);
         const uint32_t cur = op0 + (uint32_t)(j & 1) * buf_bytes;
@@ -752,11 +887,25 @@ hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out)
     int bestNW = 1;
     double best_score = -1.0;
     std::vector<std::vector<int>> best_lists;
-    for (int NW = std::min(32, T); NW >= 1; --NW) {
+    // When a warp owns at most `cap` tuples (cap = 1, 2, 4, with at most
+    // reg_threads(cap, bf16) threads) the state stays in registers; such assignments
+    // are preferred whenever one exists, else warps are unconstrained.
+    std::vector<std::pair<int, int>> cand;   // (NW, cap)
+    for (int cap : {1, 2, 4})
+        for (int NW = std::min(reg_threads(cap, prec == HQA_PREC_BF16) / 32, T);
+             NW >= (T + cap - 1) / cap && NW >= 1; --NW)
+            cand.push_back({NW, cap});
+    const bool reg = !cand.empty();
+    if (!reg)
+        for (int NW = std::min(32, T); NW >= 1; --NW) cand.push_back({NW, 0});
+    for (const auto& nc : cand) {
+        const int NW = nc.first, cap = nc.second;
         std::vector<int64_t> ld(NW, 0);
         std::vector<std::vector<int>> lists(NW);
         for (int t : order) {
-            const int w = (int)(std::min_element(ld.begin(), ld.end()) - ld.begin());
+            int w = -1;
+            for (int c = 0; c < NW; ++c)
+                if ((cap == 0 || (int)lists[c].size() < cap) && (w < 0 || ld[c] < ld[w])) w = c;
             ld[w] += tups[t].K;
             lists[w].push_back(t);
         }
@@ -771,7 +920,9 @@ hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out)
     }
     std::vector<int> woff(bestNW + 1, 0), tlist;
     int64_t mk = 1;
+    int max_wt = 0;
     for (int w = 0; w < bestNW; ++w) {
+        max_wt = std::max(max_wt, (int)best_lists[w].size());
         int64_t ld = 0;
         for (int t : best_lists[w]) {
             tlist.push_back(t);
@@ -792,6 +943,7 @@ hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out)
     pl.NW = bestNW;
     pl.ent_bytes = ent_bytes;
     pl.balance = (double)total / ((double)bestNW * (double)mk);
+    pl.max_wt = max_wt;
     pl.pad_ratio = ctx->nnz > 0 ? (double)stored / (double)ctx->nnz : 0.0;
     pl.conflict_ratio = ideal > 0 ? (double)wave / (double)ideal : 1.0;
     HQA_CUDA_TRY(cudaMalloc(&pl.d_entries, ent_bytes));
@@ -815,9 +967,22 @@ hqa_status hqa_vec_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out)
 template <int RB, bool BF16>
 static cudaError_t launch_vec_md(const VArgs& a, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = hqa_smem_attr((const void*)k_sparse_md_vec<RB, BF16>, smem);
+    if (a.reg) {
+        if (threads > reg_threads(a.reg, BF16)) return cudaErrorInvalidValue;
+        const void* fn = a.reg == 1 ? (const void*)k_sparse_md_vec<RB, BF16, 1>
+                       : a.reg == 2 ? (const void*)k_sparse_md_vec<RB, BF16, 2>
+                                    : (const void*)k_sparse_md_vec<RB, BF16, 4>;
+        cudaError_t e = hqa_smem_attr(fn, smem);
+        if (e != cudaSuccess) return e;
+        const int blocks = (a.R + RB - 1) / RB;
+        if (a.reg == 1) k_sparse_md_vec<RB, BF16, 1><<<blocks, threads, smem, st>>>(a);
+        else if (a.reg == 2) k_sparse_md_vec<RB, BF16, 2><<<blocks, threads, smem, st>>>(a);
+        else k_sparse_md_vec<RB, BF16, 4><<<blocks, threads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    cudaError_t e = hqa_smem_attr((const void*)k_sparse_md_vec<RB, BF16, 0>, smem);
     if (e != cudaSuccess) return e;
-    k_sparse_md_vec<RB, BF16><<<(a.R + RB - 1) / RB, threads, smem, st>>>(a);
+    k_sparse_md_vec<RB, BF16, 0><<<(a.R + RB - 1) / RB, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -887,6 +1052,10 @@ hqa_status hqa_vec_launch_md(hqa_ctx* ctx, const SparsePlan* pl, const StepCoef*
     a.p_out = p_out;
     a.phibar_out = phibar_out;
     a.gwin = static_cast<float*>(ctx->d_state);
+    a.reg = 0;
+    for (int r : {1, 2, 4})
+        if (a.reg == 0 && pl->max_wt <= r && pl->NW * 32 <= reg_threads(r, pl->prec == HQA_PREC_BF16))
+            a.reg = r;
     a.seed = seed;
     a.S = S;
     a.W = W;

@@ -77,7 +77,7 @@ class PlanInfo(C.Structure):
     _fields_ = [
         ("kernel", C.c_int32), ("replicas_per_block", C.c_int32), ("blocks", C.c_int32),
         ("threads", C.c_int32), ("smem_bytes", C.c_int64), ("pad_ratio", C.c_double),
-        ("conflict_ratio", C.c_double), ("balance", C.c_double),
+        ("conflict_ratio", C.c_double), ("balance", C.c_double), ("chunks", C.c_int32),
     ]
 
 
