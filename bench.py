@@ -79,6 +79,27 @@ def make_instance(name):
     raise KeyError(name)
 
 
+def shard_seed(rank):
+    """Stream seed of one rank's replicas: ranks run disjoint, independent shards."""
+    return 1000 + rank * 100003
+
+
+def reduce_max(values, ws):
+    """Per-rank totals -> their maximum over ranks (gloo or NCCL all-reduce)."""
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(units_per_rank_step, steps, ws, total_time):
+    """Units processed by all ranks / the slowest rank's time."""
+    return units_per_rank_step * steps * ws / total_time
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -230,7 +251,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
-    seed_base = 1000 + rank * 100003
+    seed_base = shard_seed(rank)
 
     RR = R * count   # per-replica results
     out = {k: torch.empty(s, dtype=d, device=dev) for k, s, d in (
@@ -354,13 +375,9 @@ def run_ours(args):
     su_step = N * R * S
     tot_pipe = sum(variants[head]["t_pipe"])
     tot_e2e = sum(t_e2e)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_pipe, tot_e2e], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_pipe, tot_e2e = float(t[0]), float(t[1])
-    value = su_step * args.steps * ws / tot_pipe
-    e2e_value = su_step * args.steps * ws / tot_e2e
+    tot_pipe, tot_e2e = reduce_max([tot_pipe, tot_e2e], ws)
+    value = whole_job_rate(su_step, args.steps, ws, tot_pipe)
+    e2e_value = whole_job_rate(su_step, args.steps, ws, tot_e2e)
 
     # roofline of the dominant kernel (the MD kernel), timed alone with CUDA events
     clk = clocks.summary()
