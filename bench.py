@@ -216,7 +216,7 @@ def kernel_name(hqa, plan, prec_name):
     k = plan["kernel"]
     if k == hqa.KERNEL_DENSE:
         split = "true" if prec_name == "PREC_BF16X2" else "false"
-        return f"k_dense_md<{plan['replicas_per_block'] // 2},4,{split}>"
+        return f"k_dense_md<{plan['replicas_per_block'] // 2},*,{split},false>"
     base = "k_sparse_md_vec" if k == hqa.KERNEL_VECTOR else "k_sparse_md"
     return f"{base}<{plan['replicas_per_block']},{'true' if prec_name == 'PREC_BF16' else 'false'}>"
 
@@ -298,7 +298,7 @@ def run_ours(args):
         for name, prec_name in cfg["variants"]:
             prec = getattr(hqa, prec_name)
             tuned = None
-            if cfg["kind"] != "dense":
+            if cfg["kind"] != "dense" and not args.no_tune:
                 # launch shape (kernel, replicas per block) by the library's autotuner
                 best, rows = ctx.autotune(R, precision=prec, probe_steps=64 if batch else min(S, 500))
                 tuned = {"kernel": best["kernel"], "replicas_per_block": best["replicas_per_block"],
@@ -383,7 +383,7 @@ def run_ours(args):
     clk = clocks.summary()
     hv = variants[head]
     if batch:
-        rb = hv["tuned"]["replicas_per_block"]
+        rb = hv["tuned"]["replicas_per_block"] if hv["tuned"] else 0
         plan = {"kernel": hqa.KERNEL_SCALAR, "replicas_per_block": rb, "members": count,
                 "note": "persistent batch kernel, replica blocking by the autotuner"}
         kname = f"k_sparse_md_batch<{rb},{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
@@ -536,6 +536,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--md-steps", type=int, default=0,
                     help="override the workload's MD step count (shorter runs for profiling)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default launch shapes (profiling: the autotuner's "
+                         "timings would see the profiler's replays)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -292,14 +292,16 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
     return v;
 }
 
-template <int NH, int STAGES, bool SPLIT>
+template <int NH, int STAGES, bool SPLIT, bool FUSED>
 __global__ void __launch_bounds__(kMDThreads, 1)
 k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
            const DenseMDArgs a)
 {
     constexpr uint32_t A_BYTES = BM * BK * 2;
     constexpr uint32_t B_BYTES = NH * BK * 2;
-    constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    // fused: one J tile per stage feeds the MMAs of both column halves
+    constexpr uint32_t STAGE_BYTES = A_BYTES + (FUSED ? 2u : 1u) * B_BYTES;
+    constexpr int NPASS = FUSED ? 1 : 2;   // MMA passes (and counters) per step
     constexpr uint32_t TMEM_COLS = 2 * NH <= 64 ? 64 : 2 * NH <= 128 ? 128 : 2 * NH <= 256 ? 256 : 512;
     static_assert(NH % 16 == 0 && NH <= 256, "UMMA N");
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
@@ -345,7 +347,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
             // ---- TMA producer ----
             uint32_t it = 0;
             for (int64_t m = 0; m < a.S && !*abort; ++m) {
-                for (int hh = 0; hh < 2 && !*abort; ++hh) {
+                for (int hh = 0; hh < NPASS && !*abort; ++hh) {
                     if (m > 0) {
                         const unsigned int* g = a.gbar + 2 * nc + hh;
                         const unsigned int target = (unsigned int)(a.Mt * m);
@@ -372,6 +374,9 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                         tc::mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
                         tc::tma_load_2d(sa, &tmJ, (kt % a.KT) * BK, m0, full0 + 8 * s);
                         tc::tma_load_2d(sa + A_BYTES, &tmB, kt * BK, brow, full0 + 8 * s);
+                        if constexpr (FUSED)
+                            tc::tma_load_2d(sa + A_BYTES + B_BYTES, &tmB, kt * BK, brow + NH,
+                                            full0 + 8 * s);
                     }
                 }
             }
@@ -386,7 +391,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
             constexpr uint32_t idesc = tc::idesc_bf16(BM, NH);
             uint32_t it = 0;
             for (int64_t m = 0; m < a.S && !*abort; ++m) {
-                for (int hh = 0; hh < 2 && !*abort; ++hh) {
+                for (int hh = 0; hh < NPASS && !*abort; ++hh) {
                     if (m > 0 && !tc::mbar_wait(acce0 + 8 * hh, (uint32_t)((m - 1) & 1), abort, kWaitNs))
                         break;
                     tc::tc_fence_after();
@@ -401,6 +406,13 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
                             tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+                        if constexpr (FUSED) {
+                            const uint64_t bd1 = tc::sdesc_k128(sa + A_BYTES + B_BYTES);
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk)
+                                tc::mma_bf16(d + (uint32_t)NH, ad + 2 * kk, bd1 + 2 * kk, idesc,
+                                             (kt | kk) != 0);
+                        }
                         tc::mma_commit(empty0 + 8 * s);
                     }
                     tc::mma_commit(accf0 + 8 * hh);
@@ -423,25 +435,46 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
             const bool in_win = m >= win0;
             const int Kb = SPLIT ? 2 * a.Npad : a.Npad;   // operand row: [hi | lo] when split
             __nv_bfloat16* nb = a.phib + (size_t)((m + 1) & 1) * a.Rpad * Kb;
+            bool ok = true;
             for (int hh = 0; hh < 2 && !stop; ++hh) {
-                const bool ok = __all_sync(0xffffffffu,
-                                           tc::mbar_wait(accf0 + 8 * hh, (uint32_t)(m & 1), abort, kWaitNs));
-                tc::tc_fence_after();
+                // the state of this warp's first chunk does not depend on the MMA:
+                // its loads are in flight while the accumulator is computed
+                float ph[16], pp[16];
+                if (row_ok && csel < NH / 16) {
+                    const int rb0 = n0 + hh * NH + csel * 16;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const size_t o = (size_t)(rb0 + j) * a.Npad + row;
+                        ph[j] = a.phi[o];
+                        pp[j] = a.p[o];
+                    }
+                }
+                const int pass = FUSED ? 0 : hh;
+                if (!FUSED || hh == 0) {
+                    ok = __all_sync(0xffffffffu,
+                                    tc::mbar_wait(accf0 + 8 * pass, (uint32_t)(m & 1), abort, kWaitNs));
+                    tc::tc_fence_after();
+                }
                 if (ok) {
 #pragma unroll 1
                     for (int c = csel; c < NH / 16; c += 2) {
                         uint32_t v[16];
                         tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(hh * NH + c * 16), v);
+                        // the next chunk's state loads overlap this chunk's update
+                        float nph[16], npp[16];
+                        const bool more = row_ok && c + 2 < NH / 16;
+                        if (more) {
+                            const int rb1 = n0 + hh * NH + (c + 2) * 16;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const size_t o = (size_t)(rb1 + j) * a.Npad + row;
+                                nph[j] = a.phi[o];
+                                npp[j] = a.p[o];
+                            }
+                        }
                         tc::tmem_wait_ld();
                         if (row_ok) {
                             const int rbase = n0 + hh * NH + c * 16;
-                            float ph[16], pp[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const size_t o = (size_t)(rbase + j) * a.Npad + row;
-                                ph[j] = a.phi[o];
-                                pp[j] = a.p[o];
-                            }
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const size_t o = (size_t)(rbase + j) * a.Npad + row;
@@ -460,12 +493,22 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                 if (in_win) a.w[o] += fn;
                             }
                         }
+                        if (more) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                ph[j] = nph[j];
+                                pp[j] = npp[j];
+                            }
+                        }
                     }
-                    // accumulator h may be overwritten once every epilogue warp has read it
-                    tc::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(acce0 + 8 * hh);
+                    // the accumulator may be overwritten once every epilogue warp has read it
+                    if (!FUSED || hh == 1) {
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(acce0 + 8 * pass);
+                    }
                 }
+                if (FUSED && hh == 0) continue;
                 // Phi^(m+1) of this half -> visible to the other CTAs' TMA loads
                 tc::fence_proxy_async_global();
                 // all epilogue warps meet here every half-step; the barrier also
@@ -480,7 +523,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     stop = true;
                 } else if (ew == 0 && lane == 0) {
                     __threadfence();
-                    atomicAdd(a.gbar + 2 * nc + hh, 1u);
+                    atomicAdd(a.gbar + 2 * nc + pass, 1u);
                 }
             }
         }
@@ -558,10 +601,27 @@ __global__ void k_dense_out(DenseMDArgs a, float inv_w, float* phi_out, float* p
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_NONFINITE);
 }
 
-template <int NH, int STAGES>
+template <int NH, int STAGES, bool FUSED>
 size_t md_smem()
 {
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + NH * BK * 2) + 16 * STAGES + 64 + 64;
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + (FUSED ? 2 : 1) * NH * BK * 2) + 16 * STAGES +
+           64 + 64;
+}
+
+// Fused halves (both column halves from one J tile per stage, which halves the
+// J stream from L2, the epilogue draining both halves after one accumulator
+// wait) measured slower on K2000 x 2048 replicas (57 vs 40 us per step): the
+// epilogue of one half no longer overlaps the MMA of the other.  Kept as an
+// option, off.
+constexpr bool kFusedHalves = false;
+
+// Ring depth: as many stages as fit in ~218 KB of shared memory, at most 4
+// (6 stages measured no faster on K2000 x 2048 replicas).
+constexpr int md_stages(int nh, bool fused)
+{
+    const int stage = BM * BK * 2 + (fused ? 2 : 1) * nh * BK * 2;
+    const int n = (218 * 1024) / stage;
+    return n > 4 ? 4 : n;
 }
 
 // Column halves: NH replicas (multiple of 16, <= 256); Nc = ceil(R / 2NH) with
@@ -590,17 +650,17 @@ template <int NH, bool SPLIT>
 static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
                                     const CUtensorMap& tmB)
 {
-    constexpr int STAGES = 4;
-    const size_t smem = md_smem<NH, STAGES>();
+    constexpr int STAGES = md_stages(NH, kFusedHalves);
+    static_assert(STAGES >= 2, "ring depth");
+    const size_t smem = md_smem<NH, STAGES, kFusedHalves>();
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     // a cooperative launch is not captured into graphs here
     if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
-    if (hqa_smem_attr((const void*)k_dense_md<NH, STAGES, SPLIT>, smem) != cudaSuccess)
-        return HQA_ERR_CUDA;
+    const void* fn = (const void*)k_dense_md<NH, STAGES, SPLIT, kFusedHalves>;
+    if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
     void* args[] = {const_cast<CUtensorMap*>(&ctx->tmJ), const_cast<CUtensorMap*>(&tmB),
                     const_cast<DenseMDArgs*>(&a)};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_dense_md<NH, STAGES, SPLIT>,
-                                                dim3(grid), dim3(kMDThreads), args, smem, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kMDThreads), args, smem, st);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
         (void)cudaGetLastError();
         return HQA_ERR_TOO_LARGE;
