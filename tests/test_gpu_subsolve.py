@@ -49,6 +49,32 @@ def test_subsolve_bit_exact(hqa, orc, inst_name, n, R):
         assert int(e[r]) == we
 
 
+def test_subsolve_packed_and_scalar_walks_mixed(hqa, orc):
+    """Replicas whose reduced energies fit in 16 bits take the packed four-lane walk,
+    the others (here: spins with fields of 20000 in the ambivalent set) the scalar
+    walk; both in one call, bit-exact against the oracle."""
+    base = instances.er_pm1(150, 0.1, 8)
+    rng = np.random.default_rng(77)
+    h = np.zeros(base.N)
+    big = rng.choice(base.N, size=15, replace=False)
+    h[big] = rng.choice([-20000.0, 20000.0], size=15)
+    inst = instances.Instance(base.name + "_bigh", base.N, None, base.row_ptr, base.col,
+                              base.val, h, dict(base.meta))
+    ctx = hqa.Context.from_instance(inst)
+    R, n = 16, 8
+    spins = rng.choice(np.array([-1, 1], np.int8), size=(R, inst.N))
+    frozen = _masks(inst.N, R, n, rng)
+    has_big = [bool(np.any(frozen[r, big] == 0)) for r in range(R)]
+    assert any(has_big) and not all(has_big)
+    out, e = ctx.solve_sub(torch.from_numpy(spins).cuda(), torch.from_numpy(frozen).cuda(), n)
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    for r in range(R):
+        ws, we, _, _ = orc.subsolve(pr, spins[r], frozen[r])
+        assert np.array_equal(out[r].cpu().numpy(), ws)
+        assert int(e[r]) == we
+
+
 def test_subsolve_n24_bit_exact(hqa, orc):
     """The configuration-5 sub-problem size: n = 24 (2^24 assignments)."""
     inst = instances.er_mean_degree_pm1(1000, 8.0, 11)
