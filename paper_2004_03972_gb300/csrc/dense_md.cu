@@ -292,7 +292,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
     return v;
 }
 
-template <int NH, int STAGES, bool SPLIT, bool FUSED>
+template <int NH, int STAGES, bool SPLIT, bool FUSED, bool ONCHIP>
 __global__ void __launch_bounds__(kMDThreads, 1)
 k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
            const DenseMDArgs a)
@@ -302,8 +302,11 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
     // fused: one J tile per stage feeds the MMAs of both column halves
     constexpr uint32_t STAGE_BYTES = A_BYTES + (FUSED ? 2u : 1u) * B_BYTES;
     constexpr int NPASS = FUSED ? 1 : 2;   // MMA passes (and counters) per step
-    constexpr uint32_t TMEM_COLS = 2 * NH <= 64 ? 64 : 2 * NH <= 128 ? 128 : 2 * NH <= 256 ? 256 : 512;
+    // on-chip state: p in TMEM columns [2 NH, 4 NH), phi in shared memory
+    constexpr uint32_t TMEM_COLS = ONCHIP ? 512u
+                                 : 2 * NH <= 64 ? 64 : 2 * NH <= 128 ? 128 : 2 * NH <= 256 ? 256 : 512;
     static_assert(NH % 16 == 0 && NH <= 256, "UMMA N");
+    static_assert(!ONCHIP || (NH <= 128 && !FUSED), "on-chip state: 4 NH TMEM columns");
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -311,6 +314,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
     const uint32_t full0 = bar, empty0 = bar + 8 * STAGES;
     const uint32_t accf0 = bar + 16 * STAGES, acce0 = accf0 + 16;
     const uint32_t tmem_slot = acce0 + 16;
+    const uint32_t phis = bar + 1024;   // ONCHIP: phi tile [2 NH columns][128 rows] FP32
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.Mt, nc = blockIdx.x / a.Mt;
@@ -429,6 +433,25 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         const float hr = (a.h && row_ok) ? 2.f * a.h[row] : 0.f;
         const int mhalf = (a.M - 2) / 2;
         const int64_t win0 = a.S - (int64_t)a.W;
+        const uint32_t tl = (uint32_t)(32 * quarter) << 16;   // this warp's TMEM lanes
+        const uint32_t rloc = (uint32_t)(32 * quarter + lane);  // row within the tile
+        if constexpr (ONCHIP) {
+            // the tile's state moves on chip for the whole trajectory
+            for (int hh = 0; hh < 2; ++hh)
+                for (int c = csel; c < NH / 16; c += 2) {
+                    const int col = hh * NH + c * 16;
+                    uint32_t pv[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const size_t o = (size_t)(n0 + col + j) * a.Npad + row;
+                        asm volatile("st.shared.f32 [%0], %1;" ::"r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u),
+                                     "f"(a.phi[o]));
+                        pv[j] = __float_as_uint(a.p[o]);
+                    }
+                    tc::tmem_st16(tmem + tl + (uint32_t)(2 * NH + col), pv);
+                }
+            tc::tmem_wait_st();
+        }
         bool stop = false;
         for (int64_t m = 0; m < a.S && !stop; ++m) {
             const float4 cf = __ldg(reinterpret_cast<const float4*>(a.sched) + m);
@@ -440,7 +463,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                 // the state of this warp's first chunk does not depend on the MMA:
                 // its loads are in flight while the accumulator is computed
                 float ph[16], pp[16];
-                if (row_ok && csel < NH / 16) {
+                if (!ONCHIP && row_ok && csel < NH / 16) {
                     const int rb0 = n0 + hh * NH + csel * 16;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -455,7 +478,46 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                     tc::mbar_wait(accf0 + 8 * pass, (uint32_t)(m & 1), abort, kWaitNs));
                     tc::tc_fence_after();
                 }
-                if (ok) {
+                if (ok && ONCHIP) {
+#pragma unroll 1
+                    for (int c = csel; c < NH / 16; c += 2) {
+                        const int col = hh * NH + c * 16;
+                        uint32_t v[16], pv[16];
+                        tc::tmem_ld16(tmem + tl + (uint32_t)col, v);
+                        tc::tmem_ld16(tmem + tl + (uint32_t)(2 * NH + col), pv);
+                        float phl[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            asm volatile("ld.shared.f32 %0, [%1];"
+                                         : "=f"(phl[j]) : "r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u));
+                        tc::tmem_wait_ld();
+                        if (row_ok) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const float L = __uint_as_float(v[j]) + hr * fabsf(phl[j]);
+                                const float phi2 = phl[j] * phl[j];
+                                float pw = phl[j];
+                                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                                const float pn = __uint_as_float(pv[j]) - fmaf(cf.x, pw, cf.y * L);
+                                const float fn = fmaf(cf.z, pn, phl[j]);
+                                pv[j] = __float_as_uint(pn);
+                                asm volatile("st.shared.f32 [%0], %1;"
+                                             ::"r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u), "f"(fn));
+                                const size_t ob = (size_t)(n0 + col + j) * Kb + row;
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(fn);
+                                nb[ob] = hi;
+                                if (SPLIT) nb[ob + a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                if (in_win) a.w[(size_t)(n0 + col + j) * a.Npad + row] += fn;
+                            }
+                        }
+                        // .sync.aligned: every lane of the warp, outside the row_ok branch
+                        tc::tmem_st16(tmem + tl + (uint32_t)(2 * NH + col), pv);
+                        tc::tmem_wait_st();
+                    }
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(acce0 + 8 * pass);
+                } else if (ok) {
 #pragma unroll 1
                     for (int c = csel; c < NH / 16; c += 2) {
                         uint32_t v[16];
@@ -526,6 +588,25 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     atomicAdd(a.gbar + 2 * nc + pass, 1u);
                 }
             }
+        }
+        if constexpr (ONCHIP) {
+            // final state back to global memory (the output kernel reads it there)
+            for (int hh = 0; hh < 2; ++hh)
+                for (int c = csel; c < NH / 16; c += 2) {
+                    const int col = hh * NH + c * 16;
+                    uint32_t pv[16];
+                    tc::tmem_ld16(tmem + tl + (uint32_t)(2 * NH + col), pv);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const size_t o = (size_t)(n0 + col + j) * a.Npad + row;
+                        float f;
+                        asm volatile("ld.shared.f32 %0, [%1];"
+                                     : "=f"(f) : "r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u));
+                        a.phi[o] = f;
+                        a.p[o] = __uint_as_float(pv[j]);
+                    }
+                }
         }
     }
     tc::tc_fence_before();
@@ -601,12 +682,18 @@ __global__ void k_dense_out(DenseMDArgs a, float inv_w, float* phi_out, float* p
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_NONFINITE);
 }
 
-template <int NH, int STAGES, bool FUSED>
+template <int NH, int STAGES, bool FUSED, bool ONCHIP>
 size_t md_smem()
 {
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + (FUSED ? 2 : 1) * NH * BK * 2) + 16 * STAGES +
-           64 + 64;
+    // alignment slack, ring, barrier block (1 KB), on-chip phi tile
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + (FUSED ? 2 : 1) * NH * BK * 2) + 1024 +
+           (ONCHIP ? (size_t)2 * NH * BM * 4 : 0);
 }
+
+// The tile's state (phi, p) stays on chip for the whole trajectory when its
+// p fits next to the accumulators in TMEM (4 NH <= 512 columns) and its phi
+// next to at least 3 ring stages in shared memory.
+constexpr bool onchip_ok(int nh) { return nh <= 128; }
 
 // Fused halves (both column halves from one J tile per stage, which halves the
 // J stream from L2, the epilogue draining both halves after one accumulator
@@ -615,12 +702,13 @@ size_t md_smem()
 // option, off.
 constexpr bool kFusedHalves = false;
 
-// Ring depth: as many stages as fit in ~218 KB of shared memory, at most 4
+// Ring depth: as many stages as fit in the 227 KB opt-in shared memory next to
+// the alignment slack, the barrier block and the on-chip phi tile, at most 4
 // (6 stages measured no faster on K2000 x 2048 replicas).
-constexpr int md_stages(int nh, bool fused)
+constexpr int md_stages(int nh, bool fused, bool onchip)
 {
     const int stage = BM * BK * 2 + (fused ? 2 : 1) * nh * BK * 2;
-    const int n = (218 * 1024) / stage;
+    const int n = (227 * 1024 - 2048 - 64 - (onchip ? 2 * nh * BM * 4 : 0)) / stage;
     return n > 4 ? 4 : n;
 }
 
@@ -650,13 +738,14 @@ template <int NH, bool SPLIT>
 static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
                                     const CUtensorMap& tmB)
 {
-    constexpr int STAGES = md_stages(NH, kFusedHalves);
+    constexpr bool ONCHIP = onchip_ok(NH) && !kFusedHalves;
+    constexpr int STAGES = md_stages(NH, kFusedHalves, ONCHIP);
     static_assert(STAGES >= 2, "ring depth");
-    const size_t smem = md_smem<NH, STAGES, kFusedHalves>();
+    const size_t smem = md_smem<NH, STAGES, kFusedHalves, ONCHIP>();
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     // a cooperative launch is not captured into graphs here
     if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
-    const void* fn = (const void*)k_dense_md<NH, STAGES, SPLIT, kFusedHalves>;
+    const void* fn = (const void*)k_dense_md<NH, STAGES, SPLIT, kFusedHalves, ONCHIP>;
     if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
     void* args[] = {const_cast<CUtensorMap*>(&ctx->tmJ), const_cast<CUtensorMap*>(&tmB),
                     const_cast<DenseMDArgs*>(&a)};
