@@ -147,7 +147,13 @@ void hqa_run_opts_default(hqa_run_opts* o);
  *          ignored (all sums in Eqs. (1), (3) run over j != i)
  *   h      host, N floats, or NULL for h = 0
  *   flags  reserved, pass 0
- * The couplings are copied; `*out` owns device copies.
+ * The couplings are copied; `*out` owns device copies, among them the
+ * tensor-core operand of J.  Precisions on a dense context (hqa_run with
+ * HQA_PREC_BF16 / HQA_PREC_BF16X2, the tcgen05 path): BF16 multiplies J and
+ * phi rounded to BF16 (J exact for +-1 couplings); BF16X2 splits phi into
+ * BF16 hi + lo and, when J is not exact in BF16 (real-valued couplings),
+ * J as well: J_hi phi_hi + J_lo phi_hi + J_hi phi_lo, about 16 significant
+ * bits of each.  FP32 runs (the CSR kernels) need couplings in {-1, 0, +1}.
  * Errors: INVALID_ARG (N out of range, null J/out), ASYMMETRIC,
  * NONFINITE_INPUT, OOM, CUDA. */
 hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t flags,
@@ -231,6 +237,14 @@ hqa_status hqa_readout(hqa_ctx* ctx, int32_t replicas, const float* phibar, int3
  * (UNSUPPORTED otherwise). */
 hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64_t* energy,
                       int64_t* cut, void* stream);
+
+/* Ising energy (Results Eq. (1)) for any real couplings and field:
+ *   E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i
+ * with J, h as given at create (FP32), every product and sum in FP64 and a
+ * fixed reduction order (the same inputs give the same bits).  spins:
+ * device [R][N] int8; energy: device [R] double.  Not for batch contexts. */
+hqa_status hqa_energy_f64(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, double* energy,
+                          void* stream);
 
 /* Exact solution of the reduced Ising problem on the ambivalent spins (HQA
  * section, Eqs. (6)-(7)).  For each replica the frozen spins keep their

@@ -345,6 +345,25 @@ int64_t or_energy_int(int32_t N, const double* J, const int64_t* row_ptr, const 
     return ordered / 2 + field;
 }
 
+/* Ising energy for real couplings and field (Results Eq. (1)), FP64:
+ *   H(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i,
+ * the pair sum taken over unordered pairs i < j directly. */
+double or_energy_f64(int32_t N, const double* J, const int64_t* row_ptr, const int32_t* col,
+                     const double* val, const double* h, const int8_t* s)
+{
+    double pair = 0.0, field = 0.0;
+    for (int32_t i = 0; i < N; ++i) {
+        if (J) {
+            for (int32_t j = i + 1; j < N; ++j) pair += J[(int64_t)i * N + j] * s[i] * s[j];
+        } else {
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+                if (col[k] > i) pair += val[k] * s[i] * s[col[k]];
+        }
+        if (h) field += h[i] * s[i];
+    }
+    return pair + field;
+}
+
 /* MAX-CUT value C(s) = 1/2 sum_{(ij) in E} w_ij (1 - s_i s_j) (Methods,
  * "MAX-CUT and Ising spin-glass"), edges = unordered pairs i < j with
  * w_ij = J_ij != 0.  Written as the edge sum itself, not via C_0. */

@@ -70,6 +70,8 @@ def _load():
             lib.or_readout.argtypes = [i32, vp, i32, vp, vp]
             lib.or_energy_int.argtypes = [i32, vp, vp, vp, vp, vp, vp]
             lib.or_energy_int.restype = i64
+            lib.or_energy_f64.argtypes = [i32, vp, vp, vp, vp, vp, vp]
+            lib.or_energy_f64.restype = d
             lib.or_cut_int.argtypes = [i32, vp, vp, vp, vp, vp]
             lib.or_cut_int.restype = i64
             lib.or_brute_force.argtypes = [i32, vp, vp, vp, vp, vp, vp]
@@ -214,6 +216,12 @@ def readout(phibar, n):
 def energy_int(pr: Problem, s):
     s = np.ascontiguousarray(s, dtype=np.int8)
     return int(_load().or_energy_int(*pr.args(), _ptr(s)))
+
+
+def energy_f64(pr: Problem, s):
+    """Ising energy for real J, h in FP64 (pair sum over i < j)."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    return float(_load().or_energy_f64(*pr.args(), _ptr(s)))
 
 
 def cut_int(pr: Problem, s):

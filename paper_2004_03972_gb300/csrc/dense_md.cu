@@ -195,26 +195,50 @@ size_t field_smem()
 
 }  // namespace
 
-// Builds the BF16 copy of J ([Mpad][Mpad], zero padded) and its tensor map.
+// Builds the BF16 tensor-core operands of J (zero padded to [Mpad][Mpad]) and
+// their tensor maps: J rounded to BF16 (exact for +-1 couplings) and, when
+// rounding is not exact (real-valued J), the split operand [J_hi | J_lo | J_hi]
+// with J_lo = BF16(J - J_hi), which with Phi split the same way gives
+// J_hi Phi_hi + J_lo Phi_hi + J_hi Phi_lo: J and Phi to ~16 significant bits.
 hqa_status hqa_dense_setup(hqa_ctx* ctx, const float* J)
 {
     const int N = ctx->N;
     const int Mpad = (N + BM - 1) / BM * BM;
     std::vector<__nv_bfloat16> jb((size_t)Mpad * Mpad, __float2bfloat16_rn(0.f));
+    std::vector<__nv_bfloat16> jl((size_t)Mpad * Mpad, __float2bfloat16_rn(0.f));
+    bool exact = true;
     for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j) {
             const float v = (i == j) ? 0.f : J[(size_t)i * N + j];
             const __nv_bfloat16 b = __float2bfloat16_rn(v);
-            if (__bfloat162float(b) != v) return HQA_OK;  // not exact in BF16: no tensor-core path
+            const float r = v - __bfloat162float(b);
+            exact = exact && r == 0.f;
             jb[(size_t)i * Mpad + j] = b;
+            jl[(size_t)i * Mpad + j] = __float2bfloat16_rn(r);
         }
     if (!get_encode()) return HQA_OK;
     void* d = nullptr;
     HQA_CUDA_TRY(cudaMalloc(&d, jb.size() * sizeof(__nv_bfloat16)));
-    HQA_CUDA_TRY(cudaMemcpy(d, jb.data(), jb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
     ctx->d_Jbf = d;
+    HQA_CUDA_TRY(cudaMemcpy(d, jb.data(), jb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
     ctx->Mpad = Mpad;
     if (!make_tmap_bf16(&ctx->tmJ, d, Mpad, Mpad, BM)) return HQA_ERR_CUDA;
+    if (!exact) {
+        std::vector<__nv_bfloat16> jc((size_t)Mpad * 3 * Mpad);
+        for (size_t i = 0; i < (size_t)Mpad; ++i)
+            for (size_t j = 0; j < (size_t)Mpad; ++j) {
+                const __nv_bfloat16 hi = jb[i * Mpad + j], lo = jl[i * Mpad + j];
+                jc[i * 3 * Mpad + j] = hi;
+                jc[i * 3 * Mpad + Mpad + j] = lo;
+                jc[i * 3 * Mpad + 2 * Mpad + j] = hi;
+            }
+        void* dc = nullptr;
+        HQA_CUDA_TRY(cudaMalloc(&dc, jc.size() * sizeof(__nv_bfloat16)));
+        ctx->d_Jcat = dc;
+        HQA_CUDA_TRY(cudaMemcpy(dc, jc.data(), jc.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        if (!make_tmap_bf16(&ctx->tmJ3, dc, Mpad, (uint64_t)3 * Mpad, BM)) return HQA_ERR_CUDA;
+    }
+    ctx->dense_exact = exact;
     ctx->dense_tc = true;
     return HQA_OK;
 }
@@ -292,7 +316,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
     return v;
 }
 
-template <int NH, int STAGES, bool SPLIT, bool FUSED, bool ONCHIP>
+template <int NH, int STAGES, int KSEG, bool FUSED, bool ONCHIP>
 __global__ void __launch_bounds__(kMDThreads, 1)
 k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
            const DenseMDArgs a)
@@ -367,8 +391,9 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                         tc::fence_proxy_async_global();
                     }
                     const int brow = (int)(m & 1) * a.Rpad + n0 + hh * NH;
-                    // split operand: K runs over [hi | lo], J is reused for both halves
-                    const int KTT = SPLIT ? 2 * a.KT : a.KT;
+                    // split operands: K runs over [hi | lo] with J reused (KSEG 2), or
+                    // over [hi | hi | lo] against [J_hi | J_lo | J_hi] (KSEG 3)
+                    const int KTT = KSEG * a.KT;
                     for (int kt = 0; kt < KTT; ++kt, ++it) {
                         const int s = it % STAGES;
                         if (it >= STAGES &&
@@ -376,7 +401,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                             break;
                         const uint32_t sa = base + s * STAGE_BYTES;
                         tc::mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-                        tc::tma_load_2d(sa, &tmJ, (kt % a.KT) * BK, m0, full0 + 8 * s);
+                        tc::tma_load_2d(sa, &tmJ, (KSEG == 2 ? kt % a.KT : kt) * BK, m0, full0 + 8 * s);
                         tc::tma_load_2d(sa + A_BYTES, &tmB, kt * BK, brow, full0 + 8 * s);
                         if constexpr (FUSED)
                             tc::tma_load_2d(sa + A_BYTES + B_BYTES, &tmB, kt * BK, brow + NH,
@@ -400,7 +425,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                         break;
                     tc::tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(hh * NH);
-                    const int KTT = SPLIT ? 2 * a.KT : a.KT;
+                    const int KTT = KSEG * a.KT;
                     for (int kt = 0; kt < KTT; ++kt, ++it) {
                         const int s = it % STAGES;
                         if (!tc::mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort, kWaitNs)) break;
@@ -456,7 +481,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         for (int64_t m = 0; m < a.S && !stop; ++m) {
             const float4 cf = __ldg(reinterpret_cast<const float4*>(a.sched) + m);
             const bool in_win = m >= win0;
-            const int Kb = SPLIT ? 2 * a.Npad : a.Npad;   // operand row: [hi | lo] when split
+            const int Kb = KSEG * a.Npad;   // operand row: [hi], [hi | lo] or [hi | hi | lo]
             __nv_bfloat16* nb = a.phib + (size_t)((m + 1) & 1) * a.Rpad * Kb;
             bool ok = true;
             for (int hh = 0; hh < 2 && !stop; ++hh) {
@@ -506,7 +531,11 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                 const size_t ob = (size_t)(n0 + col + j) * Kb + row;
                                 const __nv_bfloat16 hi = __float2bfloat16_rn(fn);
                                 nb[ob] = hi;
-                                if (SPLIT) nb[ob + a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                if (KSEG == 2) nb[ob + a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                if (KSEG == 3) {
+                                    nb[ob + a.Npad] = hi;
+                                    nb[ob + 2 * a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                }
                                 if (in_win) a.w[(size_t)(n0 + col + j) * a.Npad + row] += fn;
                             }
                         }
@@ -551,7 +580,11 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                 const size_t ob = (size_t)(rbase + j) * Kb + row;
                                 const __nv_bfloat16 hi = __float2bfloat16_rn(fn);
                                 nb[ob] = hi;
-                                if (SPLIT) nb[ob + a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                if (KSEG == 2) nb[ob + a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                if (KSEG == 3) {
+                                    nb[ob + a.Npad] = hi;
+                                    nb[ob + 2 * a.Npad] = __float2bfloat16_rn(fn - __bfloat162float(hi));
+                                }
                                 if (in_win) a.w[o] += fn;
                             }
                         }
@@ -621,9 +654,9 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
 // State set-up: phi(0), p(0) (SplitMix64 or caller-given), window 0, BF16
 // operand buffer 0; padding rows/replicas zero in every array.
 __global__ void k_dense_init(DenseMDArgs a, uint64_t seed, int init, const float* phi0,
-                             const float* p0, int split)
+                             const float* p0, int kseg)
 {
-    const int Kb = split ? 2 * a.Npad : a.Npad;
+    const int Kb = kseg * a.Npad;
     const size_t total = (size_t)a.Rpad * a.Npad;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -657,9 +690,15 @@ __global__ void k_dense_init(DenseMDArgs a, uint64_t seed, int init, const float
         const __nv_bfloat16 hi = __float2bfloat16_rn(phi);
         a.phib[ob] = hi;
         a.phib[buf + ob] = __float2bfloat16_rn(0.f);
-        if (split) {
+        if (kseg == 2) {
             a.phib[ob + a.Npad] = __float2bfloat16_rn(phi - __bfloat162float(hi));
             a.phib[buf + ob + a.Npad] = __float2bfloat16_rn(0.f);
+        }
+        if (kseg == 3) {
+            a.phib[ob + a.Npad] = hi;
+            a.phib[ob + 2 * a.Npad] = __float2bfloat16_rn(phi - __bfloat162float(hi));
+            a.phib[buf + ob + a.Npad] = __float2bfloat16_rn(0.f);
+            a.phib[buf + ob + 2 * a.Npad] = __float2bfloat16_rn(0.f);
         }
     }
 }
@@ -734,9 +773,9 @@ int pick_nh(int Mt, int R, int sms)
 
 }  // namespace
 
-template <int NH, bool SPLIT>
+template <int NH, int KSEG>
 static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
-                                    const CUtensorMap& tmB)
+                                    const CUtensorMap& tmA, const CUtensorMap& tmB)
 {
     constexpr bool ONCHIP = onchip_ok(NH) && !kFusedHalves;
     constexpr int STAGES = md_stages(NH, kFusedHalves, ONCHIP);
@@ -745,9 +784,9 @@ static hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     // a cooperative launch is not captured into graphs here
     if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
-    const void* fn = (const void*)k_dense_md<NH, STAGES, SPLIT, kFusedHalves, ONCHIP>;
+    const void* fn = (const void*)k_dense_md<NH, STAGES, KSEG, kFusedHalves, ONCHIP>;
     if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
-    void* args[] = {const_cast<CUtensorMap*>(&ctx->tmJ), const_cast<CUtensorMap*>(&tmB),
+    void* args[] = {const_cast<CUtensorMap*>(&tmA), const_cast<CUtensorMap*>(&tmB),
                     const_cast<DenseMDArgs*>(&a)};
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kMDThreads), args, smem, st);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
@@ -765,16 +804,20 @@ bool hqa_dense_md_possible(const hqa_ctx* ctx, int32_t R)
 
 namespace {
 
+// K segments of the tensor-core product: 1 (BF16 operand), 2 (split Phi
+// against an exact J, J reused), 3 (split Phi against a split real-valued J).
+int kseg_of(const hqa_ctx* ctx, bool split) { return split ? (ctx->dense_exact ? 2 : 3) : 1; }
+
 // Bytes one step touches for R replicas: FP32 phi and p, the two BF16 operand
-// buffers (doubled for the split operand) and the coupling operand.
-size_t dense_step_bytes(const hqa_ctx* ctx, int32_t R, bool split)
+// buffers (kseg segments each) and the coupling operand.
+size_t dense_step_bytes(const hqa_ctx* ctx, int32_t R, int kseg)
 {
     int NH = 0, grid = 0;
     if (!hqa_dense_md_geometry(ctx, R, &NH, &grid)) return SIZE_MAX;
     const size_t Rpad = (size_t)(grid / (ctx->Mpad / BM)) * 2 * NH;
     const size_t n = Rpad * (size_t)ctx->Mpad;
-    const size_t J = (size_t)ctx->Mpad * ctx->Mpad * 2 * (split ? 2 : 1);
-    return n * (8 + (split ? 8 : 4)) + J;
+    const size_t J = (size_t)ctx->Mpad * ctx->Mpad * 2 * (kseg == 3 ? 3 : 1);
+    return n * (8 + 4 * (size_t)kseg) + J;
 }
 
 // Replica chunks run one after another, each a full trajectory.  A CTA's step
@@ -785,6 +828,7 @@ size_t dense_step_bytes(const hqa_ctx* ctx, int32_t R, bool split)
 // every step, which about doubles the step.  C minimises the sum over chunks.
 int dense_chunks(const hqa_ctx* ctx, int32_t R, bool split)
 {
+    const int kseg = kseg_of(ctx, split);
     const double budget = 0.7 * (double)(ctx->l2_bytes ? ctx->l2_bytes : (size_t)96 << 20);
     int best = 1;
     double best_t = 1e300;
@@ -792,8 +836,8 @@ int dense_chunks(const hqa_ctx* ctx, int32_t R, bool split)
         const int Rc = (R + C - 1) / C;
         int NH = 0, grid = 0;
         if (!hqa_dense_md_geometry(ctx, Rc, &NH, &grid)) continue;
-        const double spill = (double)dense_step_bytes(ctx, Rc, split) > budget ? 2.0 : 1.0;
-        const double t = (double)C * ((split ? 2.0 : 1.0) * NH + 150.0) * spill;
+        const double spill = (double)dense_step_bytes(ctx, Rc, kseg) > budget ? 2.0 : 1.0;
+        const double t = (double)C * ((double)kseg * NH + 150.0) * spill;
         if (t < best_t - 1e-9) {
             best_t = t;
             best = C;
@@ -827,7 +871,8 @@ static hqa_status dense_md_chunk(hqa_ctx* ctx, const StepCoef* d_sched, int64_t 
     const int Rpad = Nc * 2 * NH;
     const int Npad = ctx->Mpad;
     const size_t n = (size_t)Rpad * Npad;
-    const size_t nb = split ? 2 * n : n;   // operand elements per buffer
+    const int kseg = kseg_of(ctx, split);
+    const size_t nb = (size_t)kseg * n;   // operand elements per buffer
     // state: phi, p, w (FP32), two BF16 operand buffers, 2 Nc counters
     const size_t off_p = n * 4, off_w = 2 * n * 4, off_b = 3 * n * 4, off_g = off_b + 2 * nb * 2;
     const size_t need = off_g + (size_t)2 * Nc * sizeof(unsigned int);
@@ -854,16 +899,18 @@ static hqa_status dense_md_chunk(hqa_ctx* ctx, const StepCoef* d_sched, int64_t 
     a.M = M;
     a.rep0 = rep0;
     CUtensorMap tmB;
-    if (!make_tmap_bf16(&tmB, a.phib, (uint64_t)2 * Rpad, split ? 2 * Npad : Npad, NH))
+    if (!make_tmap_bf16(&tmB, a.phib, (uint64_t)2 * Rpad, (uint64_t)kseg * Npad, NH))
         return HQA_ERR_CUDA;
+    const CUtensorMap& tmA = kseg == 3 ? ctx->tmJ3 : ctx->tmJ;
     k_dense_init<<<std::min<size_t>(8192, (n + 255) / 256), 256, 0, st>>>(a, seed, init, phi0, p0,
-                                                                         split ? 1 : 0);
+                                                                         kseg);
     if (cudaMemsetAsync(a.gbar, 0, (size_t)2 * Nc * sizeof(unsigned int), st) != cudaSuccess)
         return HQA_ERR_CUDA;
 #define HQA_NH_CASE(V)                                                                        \
     case V:                                                                                    \
-        s = split ? launch_dense_md_t<V, true>(ctx, a, grid, st, tmB)                          \
-                  : launch_dense_md_t<V, false>(ctx, a, grid, st, tmB);                        \
+        s = kseg == 3 ? launch_dense_md_t<V, 3>(ctx, a, grid, st, tmA, tmB)                    \
+          : kseg == 2 ? launch_dense_md_t<V, 2>(ctx, a, grid, st, tmA, tmB)                    \
+                      : launch_dense_md_t<V, 1>(ctx, a, grid, st, tmA, tmB);                   \
         break;
     switch (NH) {
         HQA_NH_CASE(256)

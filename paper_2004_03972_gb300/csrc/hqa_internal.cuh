@@ -163,6 +163,12 @@ struct hqa_ctx {
     void* d_Jbf = nullptr;         // [Mpad][Mpad] BF16, zero padded
     int Mpad = 0;
     CUtensorMap tmJ;               // TMA map of d_Jbf, 128 x 64 boxes
+    // J exactly representable in BF16 (e.g. +-1); otherwise d_Jbf holds J rounded
+    // to BF16 and d_Jcat the three-segment operand [J_hi | J_lo | J_hi] of the
+    // split product J_hi Phi_hi + J_lo Phi_hi + J_hi Phi_lo
+    bool dense_exact = false;
+    void* d_Jcat = nullptr;        // [Mpad][3 Mpad] BF16 (non-exact J only)
+    CUtensorMap tmJ3;
 };
 
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;

@@ -142,6 +142,36 @@ __global__ void __launch_bounds__(kThreads) k_energy_csr(const int32_t* __restri
                  cut ? cut + r : nullptr);
 }
 
+// Ising energy in FP64 for real-valued couplings and fields (Results Eq. (1)):
+// one block per replica, E = sum_i s_i (h_i + 1/2 sum_j J_ij s_j), each row sum
+// and each thread's partial in FP64, then a fixed-shape reduction (warp
+// shuffles, warps in order), so the result does not depend on timing.
+__global__ void __launch_bounds__(kThreads) k_energy_f64(const int32_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const float* __restrict__ val,
+                                                         const float* __restrict__ h, int N,
+                                                         const int8_t* __restrict__ spins,
+                                                         double* __restrict__ energy)
+{
+    const int r = blockIdx.x;
+    const int8_t* s = spins + (size_t)r * N;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double g = 0.0;
+        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) g += (double)val[k] * (double)s[col[k]];
+        acc += (double)s[i] * (0.5 * g + (h ? (double)h[i] : 0.0));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double sh[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        energy[r] = t;
+    }
+}
+
 // Batch of instances: block b is replica b % R of instance b / R; each
 // instance's arrays start at R * off[k] (spin-indexed) or R * k (per replica).
 __global__ void __launch_bounds__(kThreads) k_readout_batch(const BatchInst* __restrict__ inst,
@@ -195,6 +225,19 @@ hqa_status hqa_launch_readout(hqa_ctx* ctx, int32_t R, const float* phibar, int3
     if (R <= 0) return HQA_OK;
     k_readout<<<R, kThreads, 0, st>>>(phibar, ctx->N, n, spins, frozen, tally, ctx->d_status);
     return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+}
+
+extern "C" hqa_status hqa_energy_f64(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                                     double* energy, void* stream)
+{
+    if (!ctx || replicas < 1 || !spins || !energy || ((uintptr_t)energy % 8))
+        return HQA_ERR_INVALID_ARG;
+    if (ctx->is_batch) return HQA_ERR_UNSUPPORTED;
+    hqa_capture_touch(ctx);
+    k_energy_f64<<<replicas, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        ctx->d_row_ptr, ctx->d_col, ctx->d_val, ctx->has_h ? ctx->d_h : nullptr, ctx->N, spins,
+        energy);
+    return hqa_capture_note(cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA);
 }
 
 hqa_status hqa_launch_energy(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,

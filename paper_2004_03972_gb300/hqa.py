@@ -35,7 +35,7 @@ EXPORTS = (
     "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
-    "hqa_autotune", "hqa_hmd",
+    "hqa_autotune", "hqa_hmd", "hqa_energy_f64",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -139,6 +139,8 @@ def lib() -> C.CDLL:
                                        C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
                                        C.POINTER(i32), vp]
             L.hqa_autotune.restype = C.c_int
+            L.hqa_energy_f64.argtypes = [vp, i32, vp, vp, vp]
+            L.hqa_energy_f64.restype = C.c_int
             L.hqa_hmd.argtypes = [vp, C.POINTER(Schedule), C.c_double, i32, vp, vp, i32, vp,
                                   C.POINTER(RunOpts), vp]
             L.hqa_hmd.restype = C.c_int
@@ -324,6 +326,15 @@ class Context:
         _check(lib().hqa_energy(self._h, R, _ptr(spins), _ptr(e), _ptr(c), _stream_ptr(stream)),
                "hqa_energy")
         return e, c
+
+    def energy_f64(self, spins, stream=None):
+        """hqa_energy_f64: FP64 Ising energies [R] for any real couplings and field."""
+        import torch
+        R = spins.shape[0]
+        e = torch.empty(R, dtype=torch.float64, device=spins.device)
+        _check(lib().hqa_energy_f64(self._h, R, _ptr(spins), _ptr(e), _stream_ptr(stream)),
+               "hqa_energy_f64")
+        return e
 
     def solve_sub(self, spins, frozen, n, stream=None, out=None):
         import torch

@@ -179,10 +179,13 @@ def torus_for_n(N: int, seed: int) -> Instance:
 
 
 def uniform_sg(N: int, seed: int) -> Instance:
+    """Fully connected spin glass, J_ij ~ U[-1, 1] (i < j, symmetric), h_i ~ U[-2, 2].
+    Values are rounded to FP32, the precision the library takes them in, so that
+    every consumer sees the same instance."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    upper = np.triu(rng.uniform(-1.0, 1.0, size=(N, N)), k=1)
+    upper = np.triu(rng.uniform(-1.0, 1.0, size=(N, N)).astype(np.float32).astype(np.float64), k=1)
     J = upper + upper.T
-    h = rng.uniform(-2.0, 2.0, size=N)
+    h = rng.uniform(-2.0, 2.0, size=N).astype(np.float32).astype(np.float64)
     return Instance(f"uniform_sg_N{N}_s{seed}", N, dense=J, h=h, meta={"kind": "uniform_sg"})
 
 

@@ -62,15 +62,18 @@ def test_dense_field_with_field_term(hqa):
     assert _field_err(inst, phi, L.cpu().numpy().astype(np.float64)) <= 2.0 ** -8
 
 
-def test_dense_path_requires_bf16_exact_couplings(hqa):
-    inst = instances.uniform_sg(64, 2)   # real-valued J: not exact in BF16
-    J = inst.dense.astype(np.float32)
-    J = (J + J.T) / 2
-    ctx = hqa.Context.from_dense(J)
+def test_real_couplings_take_the_tensor_core_path_only(hqa):
+    """Real-valued J (not exact in BF16): the FP32 CSR kernels need couplings in
+    {-1, 0, +1} and refuse; the tensor-core field runs with J rounded to BF16."""
+    inst = instances.uniform_sg(64, 2)
+    ctx = hqa.Context.from_instance(inst)
     phi = torch.zeros((2, 64), device="cuda")
     with pytest.raises(hqa.HQAError) as ei:
-        ctx.local_field(phi, precision=hqa.PREC_BF16, kernel=hqa.KERNEL_DENSE)
+        ctx.local_field(phi, precision=hqa.PREC_FP32)
     assert ei.value.status == 6
+    L = ctx.local_field(phi, precision=hqa.PREC_BF16, kernel=hqa.KERNEL_DENSE)
+    ctx.sync()
+    assert torch.all(L == 0)
 
 
 def _close(gpu, ref, tol, scale=None):

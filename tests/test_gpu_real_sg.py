@@ -1,0 +1,123 @@
+"""Real-valued spin glass (J_ij ~ U[-1, 1], h_i ~ U[-2, 2], fully connected; Results
+"HQA for Ising spin-glass") on the tensor-core path, against the FP64 oracle.
+
+J is not exact in BF16.  Stated errors (a CPU emulation of the same rounding with
+everything else in FP64, 100 steps, dt = 1e-4; bounds are about twice that):
+  BF16    (J and phi rounded to BF16): states off by 0.27 %, 0.95 %, 3.7 % at
+          N = 100, 300, 1000 -> bounds 1e-2, 2.5e-2, 1e-1
+  BF16X2  (J_hi phi_hi + J_lo phi_hi + J_hi phi_lo): 4e-6, 1.3e-5, 7e-5 of rounding,
+          plus FP32 state arithmetic -> bounds 1e-4, 1e-4, 3e-4
+  field   (BF16): e_i <= 2^-8 of the conditioning scale (two BF16 roundings)
+Energies are FP64: within 1e-12 of the oracle's on the scale sum |J_ij| + sum |h_i|."""
+import numpy as np
+import pytest
+
+from paper_2004_03972_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hqa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_03972_gb300 import build, hqa as H
+    build.build()
+    return H
+
+
+def test_field_bf16(hqa, orc):
+    inst = instances.uniform_sg(300, 5)
+    ctx = hqa.Context.from_instance(inst)
+    rng = np.random.default_rng(3)
+    phi = rng.uniform(-1.5, 1.5, size=(40, inst.N)).astype(np.float32)
+    L = ctx.local_field(torch.from_numpy(phi).cuda(), precision=hqa.PREC_BF16,
+                        kernel=hqa.KERNEL_DENSE).cpu().numpy().astype(np.float64)
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    absJ = np.abs(inst.dense)
+    for r in range(0, 40, 7):
+        x = phi[r].astype(np.float64)
+        ref = orc.beta_field(pr, x)
+        scale = np.abs(ref) + absJ @ np.abs(x) + 2 * np.abs(inst.h) * np.abs(x)
+        assert np.max(np.abs(L[r] - ref) / scale) <= 2.0 ** -8
+
+
+def _close(gpu, ref, tol, scale=None):
+    s = np.max(np.abs(ref)) if scale is None else max(scale, np.max(np.abs(ref)))
+    return np.max(np.abs(gpu - ref)) <= tol * s
+
+
+@pytest.mark.parametrize("N,R,prec,tol", [
+    (100, 8, 1, 1e-2), (300, 64, 1, 2.5e-2), (1000, 130, 1, 1e-1),
+    (100, 8, 2, 1e-4), (300, 64, 2, 1e-4), (1000, 130, 2, 3e-4)])
+def test_states_after_100_steps(hqa, orc, N, R, prec, tol):
+    inst = instances.uniform_sg(N, 7 + N)
+    ctx = hqa.Context.from_instance(inst)
+    dt = 1.0 / 10000
+    out = ctx.run(100, R, seed=21, dt=dt, precision=prec, kernel=hqa.KERNEL_DENSE,
+                  outputs=("phi", "p", "phibar"))
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    for r in sorted({0, R // 2, R - 1}):
+        ophi, op, opbar = orc.md_run(pr, 100, dt=dt, p0=orc.initial_momenta(21, r, N))
+        assert _close(out["phi"][r].cpu().numpy(), ophi, tol)
+        assert _close(out["p"][r].cpu().numpy(), op, tol, scale=1.0)
+        assert _close(out["phibar"][r].cpu().numpy(), opbar, tol, scale=np.max(np.abs(ophi)))
+
+
+def test_energy_f64(hqa, orc):
+    inst = instances.uniform_sg(500, 9)
+    ctx = hqa.Context.from_instance(inst)
+    out = ctx.run(300, 16, seed=4, precision=hqa.PREC_BF16X2, outputs=("phibar", "spins"))
+    rng = np.random.default_rng(1)
+    rand = torch.from_numpy(rng.choice(np.array([-1, 1], np.int8), size=(16, inst.N))).cuda()
+    pr = orc.Problem.from_instance(inst)
+    scale = np.abs(np.triu(inst.dense, 1)).sum() + np.abs(inst.h).sum()
+    for spins in (out["spins"], rand):
+        e = ctx.energy_f64(spins).cpu().numpy()
+        e2 = ctx.energy_f64(spins).cpu().numpy()
+        assert np.array_equal(e, e2)                      # fixed reduction order
+        s = spins.cpu().numpy()
+        for r in range(16):
+            assert abs(e[r] - orc.energy_f64(pr, s[r])) <= 1e-12 * scale
+    # the readout of the run is better than random configurations
+    assert np.median(ctx.energy_f64(out["spins"]).cpu().numpy()) < np.median(
+        ctx.energy_f64(rand).cpu().numpy())
+
+
+def test_energy_f64_equals_integer_energy(hqa):
+    inst = instances.with_integer_field(instances.er_pm1(400, 0.05, 2), 3, 4)
+    ctx = hqa.Context.from_instance(inst)
+    rng = np.random.default_rng(2)
+    s = torch.from_numpy(rng.choice(np.array([-1, 1], np.int8), size=(9, inst.N))).cuda()
+    ei, _ = ctx.energy(s)
+    ef = ctx.energy_f64(s)
+    ctx.sync()
+    assert torch.equal(ef, ei.double())
+
+
+def test_integer_only_steps_refuse_real_couplings(hqa):
+    inst = instances.uniform_sg(120, 1)
+    ctx = hqa.Context.from_instance(inst)
+    s = torch.ones((2, inst.N), dtype=torch.int8, device="cuda")
+    f = torch.ones((2, inst.N), dtype=torch.uint8, device="cuda")
+    for call in (lambda: ctx.energy(s), lambda: ctx.solve_sub(s, f, 4)):
+        with pytest.raises(hqa.HQAError) as ei:
+            call()
+        assert ei.value.status == 6
+
+
+def test_large_replica_count_runs_in_chunks(hqa, orc):
+    """K2000-sized real spin glass: the split-J operand doubles the coupling bytes,
+    the chunk count adapts; the first replicas equal a small run's."""
+    inst = instances.uniform_sg(2000, 11)
+    ctx = hqa.Context.from_instance(inst)
+    plan = ctx.plan(4096, precision=hqa.PREC_BF16X2)
+    assert plan["kernel"] == hqa.KERNEL_DENSE and plan["chunks"] >= 2
+    big = ctx.run(20, 4096, seed=3, precision=hqa.PREC_BF16X2, outputs=("phi",))
+    small = ctx.run(20, 128, seed=3, precision=hqa.PREC_BF16X2, outputs=("phi",))
+    ctx.sync()
+    a, b = big["phi"][:128].cpu().numpy(), small["phi"].cpu().numpy()
+    assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.abs(b).max())

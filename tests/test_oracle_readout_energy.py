@@ -170,3 +170,27 @@ def test_readout_cut_never_beats_optimum(orc):
         s, _ = orc.readout(pbar, 0)
         assert orc.cut_int(pr, s) <= c_opt
         assert orc.energy_int(pr, s) >= e_opt
+
+
+def test_energy_f64_pins(orc):
+    """FP64 energy for real couplings: equals the int64 energy on integer instances;
+    Z2 symmetry at h = 0; flipping spin k changes it by -2 s_k (sum_j J_kj s_j + h_k),
+    with the field sum from the independent beta_field routine (which adds 2 h |s|)."""
+    from paper_2004_03972_gb300 import instances
+    ints = instances.with_integer_field(instances.er_pm1(90, 0.1, 4), 3, 5)
+    pr = orc.Problem.from_instance(ints)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        s = rng.choice(np.array([-1, 1], np.int8), size=ints.N)
+        assert orc.energy_f64(pr, s) == float(orc.energy_int(pr, s))
+    sg = instances.uniform_sg(70, 3)
+    pg = orc.Problem.from_instance(sg)
+    p0 = orc.Problem(sg.N, J=sg.dense)          # h = 0
+    s = rng.choice(np.array([-1, 1], np.int8), size=sg.N)
+    assert orc.energy_f64(p0, s) == pytest.approx(orc.energy_f64(p0, -s), rel=1e-14, abs=1e-12)
+    e = orc.energy_f64(pg, s)
+    g = orc.beta_field(pg, s.astype(np.float64)) - 2.0 * sg.h     # sum_j J_kj s_j
+    for k in (0, 17, 69):
+        t = s.copy()
+        t[k] = -t[k]
+        assert orc.energy_f64(pg, t) - e == pytest.approx(-2.0 * s[k] * (g[k] + sg.h[k]), abs=1e-9)
