@@ -52,6 +52,12 @@ CONFIGS = {
                    R=4096, S=10000, n=24, kind="dense", sched="paper",
                    variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
                    cpu_steps=200),
+    "sg2000": dict(desc="uniform spin glass N=2000 (J ~ U[-1,1] fully connected, h ~ U[-2,2]), "
+                        "4096 replicas, 10000 steps, paper schedule, tcgen05 field; quality = "
+                        "FP64 Ising energy of the readout (no sub-solve: real couplings)",
+                   R=4096, S=10000, n=24, kind="dense_sg", sched="paper",
+                   variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
+                   cpu_steps=200),
     "uneven512": dict(desc="512 instances, N uniform in [200,5000], half random 3-regular, half "
                            "2-D tori, +-1, 64 replicas each, 5000 steps, one persistent batch launch",
                       R=64, S=5000, n=24, kind="batch", sched="paper",
@@ -74,6 +80,8 @@ def make_instance(name):
         return instances.sk_pm1(2000, 1300)
     if name == "sk100":
         return instances.sk_pm1(100, 1100)
+    if name == "sg2000":
+        return instances.uniform_sg(2000, 1350)
     if name == "uneven512":
         return instances.uneven_batch(512, 200, 5000, 1400)
     raise KeyError(name)
@@ -216,7 +224,7 @@ def kernel_name(hqa, plan, prec_name):
     k = plan["kernel"]
     if k == hqa.KERNEL_DENSE:
         split = "true" if prec_name == "PREC_BF16X2" else "false"
-        return f"k_dense_md<{plan['replicas_per_block'] // 2},*,{split},false>"
+        return f"k_dense_md<{plan['replicas_per_block'] // 2},*,{split}>"
     base = "k_sparse_md_vec" if k == hqa.KERNEL_VECTOR else "k_sparse_md"
     return f"{base}<{plan['replicas_per_block']},{'true' if prec_name == 'PREC_BF16' else 'false'}>"
 
@@ -254,17 +262,21 @@ def run_ours(args):
     seed_base = shard_seed(rank)
 
     RR = R * count   # per-replica results
+    real = cfg["kind"] == "dense_sg"   # real couplings: FP64 energy, no integer cut or sub-solve
     out = {k: torch.empty(s, dtype=d, device=dev) for k, s, d in (
         ("phi", (R, N), torch.float32), ("p", (R, N), torch.float32),
         ("phibar", (R, N), torch.float32), ("spins", (R, N), torch.int8),
         ("frozen", (R, N), torch.uint8), ("energy", (RR,), torch.int64),
-        ("cut", (RR,), torch.int64), ("tally", (RR, 2), torch.int32))}
+        ("cut", (RR,), torch.int64), ("tally", (RR, 2), torch.int32))
+        if not (real and k in ("energy", "cut"))}
 
     sub_out = (torch.empty((R, N), dtype=torch.int8, device=dev),
                torch.empty((R,), dtype=torch.int64, device=dev))
 
     def pipeline(prec, seed, st=None):
         ctx.run(S, R, seed=seed, sched=sched, precision=prec, out=out, stream=st)
+        if real:
+            return ctx.energy_f64(out["spins"], stream=st)
         if batch:
             return None   # the batch pipeline ends at readout + energy (no batched sub-solve)
         return ctx.solve_sub(out["spins"], out["frozen"], n, stream=st, out=sub_out)
@@ -298,7 +310,7 @@ def run_ours(args):
         for name, prec_name in cfg["variants"]:
             prec = getattr(hqa, prec_name)
             tuned = None
-            if cfg["kind"] != "dense" and not args.no_tune:
+            if cfg["kind"] not in ("dense", "dense_sg") and not args.no_tune:
                 # launch shape (kernel, replicas per block) by the library's autotuner
                 best, rows = ctx.autotune(R, precision=prec, probe_steps=64 if batch else min(S, 500))
                 tuned = {"kernel": best["kernel"], "replicas_per_block": best["replicas_per_block"],
@@ -309,14 +321,17 @@ def run_ours(args):
             cuts = []
             for k in range(args.steps):
                 ctx.run(S, R, seed=seed_base + 7 * k, sched=sched, precision=prec, out=out)
-                cuts.append(out["cut"].cpu().numpy().copy())
+                if real:   # quality: minus the FP64 energy (higher is better, like a cut)
+                    cuts.append(-ctx.energy_f64(out["spins"]).cpu().numpy())
+                else:
+                    cuts.append(out["cut"].cpu().numpy().copy())
             ctx.sync()
             allcuts = np.concatenate(cuts)
             md_out = {"phibar": out["phibar"]}   # MD kernel alone (roofline timing)
             t_md = timed(lambda k, prec=prec: ctx.run(S, R, seed=seed_base + k, sched=sched,
                                                       precision=prec, out=md_out), args.steps, 1)
             t_graph = None
-            if cfg["kind"] != "dense":
+            if cfg["kind"] not in ("dense", "dense_sg"):
                 # the same step as one CUDA-graph replay (fixed seed: the replay recomputes
                 # the whole run from the seeded initial state every time)
                 gs = torch.cuda.Stream(device=dev)
@@ -350,10 +365,20 @@ def run_ours(args):
         host_spins = torch.empty((R, N), dtype=torch.int8).pin_memory()
         host_e = torch.empty((RR,), dtype=torch.int64).pin_memory()
         host_c = torch.empty((RR,), dtype=torch.int64).pin_memory()
+        host_f = torch.empty((RR,), dtype=torch.float64).pin_memory()
         d_p0 = torch.empty((R, N), dtype=torch.float32, device=dev)
         d_phi0 = torch.empty((R, N), dtype=torch.float32, device=dev)
 
         def e2e_step(k):
+            if real:
+                d_p0.copy_(pin_p0, non_blocking=True)
+                d_phi0.copy_(pin_phi0, non_blocking=True)
+                ctx.run(S, R, sched=sched, precision=best_prec, init=hqa.INIT_GIVEN, phi0=d_phi0,
+                        p0=d_p0, out=out)
+                e = ctx.energy_f64(out["spins"])
+                host_spins.copy_(out["spins"], non_blocking=True)
+                host_f.copy_(e, non_blocking=True)
+                return
             if batch:   # seeds drive the batch's initial state: H2D of the run parameters only
                 ctx.run(S, R, seed=seed_base + 11 * k, sched=sched, precision=best_prec, out=out)
                 host_spins.copy_(out["spins"], non_blocking=True)
@@ -391,10 +416,11 @@ def run_ours(args):
         plan = ctx.plan(R, precision=hv["prec"])
         kname = kernel_name(hqa, plan, hv["prec_name"])
     t_md = float(np.mean(hv["t_md"]))
-    if cfg["kind"] == "dense":
+    if cfg["kind"] in ("dense", "dense_sg"):
         pk = measured_peaks()
         flops = 2.0 * N * N * R * S                     # algorithmic: the field GEMM
-        mma = flops * (2 if hv["prec_name"] == "PREC_BF16X2" else 1)
+        kseg = (3 if real else 2) if hv["prec_name"] == "PREC_BF16X2" else 1
+        mma = flops * kseg                              # issued: one MMA pass per K segment
         achieved = flops / t_md / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"],
                 "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
@@ -417,7 +443,8 @@ def run_ours(args):
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
     # launches per pipeline step: MD (+ init and output copy on the dense path),
     # readout, energy, sub-solve (prep, enumeration, assemble, energy)
-    launches = (3 if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + (0 if batch else 4)
+    launches = (3 * plan.get("chunks", 1) if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + \
+        (0 if batch or real else 4)
     line = {
         "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_pipe / args.steps,
@@ -443,7 +470,7 @@ def run_ours(args):
                               "reaches 0", "plain": cfg["plain"]},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s",
                 "h2d_bytes_per_step": 0 if batch else 2 * R * N * 4,
-                "d2h_bytes_per_step": R * N + 2 * RR * 8},
+                "d2h_bytes_per_step": R * N + (1 if real else 2) * RR * 8},
         "gpu_launches": launches * args.steps,
         "roofline": roof,
         "clocks": clk,
