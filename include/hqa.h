@@ -366,6 +366,20 @@ hqa_status hqa_surrogate_readout(hqa_ctx* ctx, int32_t replicas, const float* lo
                                  float max_expected_errors, int8_t* spins, uint8_t* frozen,
                                  uint8_t* accept, float* expected_errors, void* stream);
 
+/* Strided snapshots of the window mean along one anneal (Results, "Sorting
+ * frozen and ambivalent variables", Fig. 4: how spins separate into frozen
+ * and ambivalent as tau grows).  The `steps` steps run as consecutive
+ * resumed segments of `stride` steps (the last may be shorter), bitwise the
+ * trajectory of one hqa_run with the same arguments; snapshot t is the
+ * window mean of segment t's last min(W, segment length) steps, so with
+ * stride >= W it equals the phibar of a run stopped after that segment.
+ * phibar_trace: device [T][R][N] float, T = ceil(steps / stride); phi, p:
+ * device [R][N], the final state (phi^(S), p^(S-1/2)).  opts->start_step
+ * must be 0.  Errors as hqa_run. */
+hqa_status hqa_run_trace(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
+                         int64_t stride, int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
+                         float* phibar_trace, float* phi, float* p, void* stream);
+
 /* MD Hamiltonian (Results, Eq. (3)) of R states as a diagnostic:
  *   H_MD = alpha(tau) sum_i (p_i^2/2 + phi_i^M)
  *        + beta(tau) (1/2 sum_ij J_ij phi_i phi_j + sum_i h_i |phi_i| phi_i),

@@ -35,7 +35,7 @@ EXPORTS = (
     "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
-    "hqa_autotune", "hqa_hmd", "hqa_energy_f64",
+    "hqa_autotune", "hqa_hmd", "hqa_energy_f64", "hqa_run_trace",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -139,6 +139,9 @@ def lib() -> C.CDLL:
                                        C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
                                        C.POINTER(i32), vp]
             L.hqa_autotune.restype = C.c_int
+            L.hqa_run_trace.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i64, i32, u64,
+                                        C.POINTER(RunOpts), vp, vp, vp, vp]
+            L.hqa_run_trace.restype = C.c_int
             L.hqa_energy_f64.argtypes = [vp, i32, vp, vp, vp]
             L.hqa_energy_f64.restype = C.c_int
             L.hqa_hmd.argtypes = [vp, C.POINTER(Schedule), C.c_double, i32, vp, vp, i32, vp,
@@ -326,6 +329,27 @@ class Context:
         _check(lib().hqa_energy(self._h, R, _ptr(spins), _ptr(e), _ptr(c), _stream_ptr(stream)),
                "hqa_energy")
         return e, c
+
+    def trace(self, steps, replicas, stride, seed=0, sched=None, dt=None, precision=PREC_FP32,
+              kernel=KERNEL_AUTO, stream=None):
+        """hqa_run_trace: (phibar snapshots [T][R][N], final phi [R][N], final p [R][N])."""
+        import torch
+        R, N = int(replicas), self.N
+        sched = sched if sched is not None else schedule()
+        opts = RunOpts()
+        lib().hqa_run_opts_default(C.byref(opts))
+        opts.precision = precision
+        opts.kernel = kernel
+        T = (int(steps) + int(stride) - 1) // int(stride)
+        dev = torch.device("cuda")
+        tr = torch.empty((T, R, N), dtype=torch.float32, device=dev)
+        phi = torch.empty((R, N), dtype=torch.float32, device=dev)
+        p = torch.empty((R, N), dtype=torch.float32, device=dev)
+        dt = (1.0 / steps) if dt is None else dt
+        _check(lib().hqa_run_trace(self._h, C.byref(sched), float(dt), int(steps), int(stride), R,
+                                   int(seed), C.byref(opts), _ptr(tr), _ptr(phi), _ptr(p),
+                                   _stream_ptr(stream)), "hqa_run_trace")
+        return tr, phi, p
 
     def energy_f64(self, spins, stream=None):
         """hqa_energy_f64: FP64 Ising energies [R] for any real couplings and field."""
