@@ -555,3 +555,76 @@ double or_mlp_loss_grad(int64_t n, const double* x, const double* y, const doubl
     }
     return loss / (double)n;
 }
+
+
+/* ------------------------------------------------------------------ */
+/* Tabu search on the reduced problem, for ambivalent sets too large to   */
+/* enumerate (the role QBSolv's tabu search plays in HQA(TS1000), HQA   */
+/* section).  Deterministic single-flip tabu search, restated here as  */
+/* the definition the GPU kernel must reproduce bit for bit:            */
+/*   f_a = h_a + sum_{j != a} J_aj s_j for ambivalent a; flipping a     */
+/*   changes the energy by d_a = -2 s_a f_a.                            */
+/*   Iteration it = 1..iters: among ambivalent a that are not tabu      */
+/*   (tabu_until[a] < it) or that would set a new best (E + d_a <       */
+/*   E_best: aspiration), take the smallest (d_a, a); flip it (even     */
+/*   uphill), update the fields of its neighbours, make it tabu until   */
+/*   it + tenure; a strictly lower E becomes the new best.              */
+/*   The best assignment (the input if nothing improves) is written to  */
+/*   spins_out; its full energy is returned.  Integer couplings only.    */
+/* ------------------------------------------------------------------ */
+int64_t or_subsolve_tabu(int32_t N, const double* J, const int64_t* row_ptr, const int32_t* col,
+                         const double* val, const double* h, const int8_t* spins_in,
+                         const uint8_t* frozen, int32_t iters, int32_t tenure, int8_t* spins_out)
+{
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    int64_t* f = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+    int64_t* until = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+    memcpy(s, spins_in, (size_t)N);
+    memcpy(spins_out, spins_in, (size_t)N);
+    for (int32_t a = 0; a < N; ++a) {
+        if (frozen[a]) continue;
+        int64_t g = h ? as_int(h[a]) : 0;
+        if (J) {
+            for (int32_t j = 0; j < N; ++j)
+                if (j != a) g += as_int(J[(int64_t)a * N + j]) * s[j];
+        } else {
+            for (int64_t k = row_ptr[a]; k < row_ptr[a + 1]; ++k)
+                if (col[k] != a) g += as_int(val[k]) * s[col[k]];
+        }
+        f[a] = g;
+    }
+    int64_t E = 0, best = 0;   /* energies relative to the input assignment */
+    for (int64_t it = 1; it <= iters; ++it) {
+        int32_t w = -1;
+        int64_t dw = 0;
+        for (int32_t a = 0; a < N; ++a) {
+            if (frozen[a]) continue;
+            const int64_t d = -2 * (int64_t)s[a] * f[a];
+            if (!(until[a] < it || E + d < best)) continue;
+            if (w < 0 || d < dw) {   /* ascending a: ties keep the smaller index */
+                w = a;
+                dw = d;
+            }
+        }
+        if (w < 0) continue;
+        s[w] = (int8_t)-s[w];
+        E += dw;
+        /* neighbours' fields: J_jw changes sign in its contribution J_jw s_w */
+        if (J) {
+            for (int32_t j = 0; j < N; ++j)
+                if (j != w) f[j] += 2 * as_int(J[(int64_t)j * N + w]) * s[w];
+        } else {
+            for (int64_t k = row_ptr[w]; k < row_ptr[w + 1]; ++k)
+                if (col[k] != w) f[col[k]] += 2 * as_int(val[k]) * s[w];
+        }
+        until[w] = it + tenure;
+        if (E < best) {
+            best = E;
+            memcpy(spins_out, s, (size_t)N);
+        }
+    }
+    free(s);
+    free(f);
+    free(until);
+    return or_energy_int(N, J, row_ptr, col, val, h, spins_out);
+}

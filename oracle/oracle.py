@@ -78,6 +78,8 @@ def _load():
             lib.or_brute_force.restype = i64
             lib.or_subsolve.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.or_subsolve.restype = i64
+            lib.or_subsolve_tabu.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp]
+            lib.or_subsolve_tabu.restype = i64
             lib.or_mlp_loss_grad.argtypes = [i64, vp, vp, vp, vp, vp]
             lib.or_mlp_loss_grad.restype = d
             _lib = lib
@@ -245,6 +247,16 @@ def subsolve(pr: Problem, spins, frozen):
     e = _load().or_subsolve(*pr.args(), _ptr(spins), _ptr(frozen), _ptr(out), C.byref(x),
                             C.byref(em))
     return out, int(e), int(x.value), int(em.value)
+
+
+def subsolve_tabu(pr: Problem, spins, frozen, iters, tenure):
+    """Deterministic tabu search on the reduced problem: (full spins, full energy)."""
+    spins = np.ascontiguousarray(spins, dtype=np.int8)
+    frozen = np.ascontiguousarray(frozen, dtype=np.uint8)
+    out = np.empty(pr.N, np.int8)
+    e = _load().or_subsolve_tabu(*pr.args(), _ptr(spins), _ptr(frozen), int(iters), int(tenure),
+                                 _ptr(out))
+    return out, int(e)
 
 
 MLP_IN, MLP_H, MLP_OUT = 6, 64, 2
