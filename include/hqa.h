@@ -265,6 +265,25 @@ hqa_status hqa_solve_sub(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
                          const uint8_t* frozen, int32_t n, int8_t* out_spins,
                          int64_t* out_energy, void* stream);
 
+/* Tabu search on the reduced problem (HQA section, Eqs. (6)-(7)) for
+ * ambivalent sets too large to enumerate (up to 1024 spins; the paper's
+ * HQA(TS1000) hands such sets to a tabu search).  Deterministic: with
+ *   f_a = h_a + sum_{j != a} J_aj s_j and d_a = -2 s_a f_a,
+ * iteration it = 1..iters flips, among ambivalent spins that are not tabu
+ * (tabu until iteration it' < it) or would give a new best energy, the one
+ * with the smallest (d_a, a) -- even uphill -- and makes it tabu until
+ * it + tenure; the best assignment met (the input if none is lower) is
+ * written to out_spins and its full energy (Eq. (1)) to out_energy (may be
+ * NULL).  spins, frozen, out_spins: device [R][N]; out_energy device [R]
+ * int64.  The ambivalent count of each replica must be <= n <= 1024 (else
+ * the input is copied and hqa_sync reports INVALID_ARG).  Integer couplings
+ * in {-1, 0, +1} and integer h (UNSUPPORTED otherwise); iters, tenure in
+ * [0, 2^30].  Not a guarantee of the optimum: hqa_solve_sub is the exact
+ * solver for n <= 30. */
+hqa_status hqa_solve_sub_tabu(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                              const uint8_t* frozen, int32_t n, int32_t iters, int32_t tenure,
+                              int8_t* out_spins, int64_t* out_energy, void* stream);
+
 /* hqa_solve_sub without any device allocation.  The paper has no
  * counterpart: this exists for callers that cannot let the library call
  * cudaMalloc -- a process whose device memory is already reserved by

@@ -35,7 +35,7 @@ EXPORTS = (
     "hqa_mlp_create", "hqa_mlp_params", "hqa_mlp_forward", "hqa_mlp_grad", "hqa_mlp_adamw",
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
-    "hqa_autotune", "hqa_hmd", "hqa_energy_f64", "hqa_run_trace",
+    "hqa_autotune", "hqa_hmd", "hqa_energy_f64", "hqa_run_trace", "hqa_solve_sub_tabu",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -139,6 +139,8 @@ def lib() -> C.CDLL:
                                        C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
                                        C.POINTER(i32), vp]
             L.hqa_autotune.restype = C.c_int
+            L.hqa_solve_sub_tabu.argtypes = [vp, i32, vp, vp, i32, i32, i32, vp, vp, vp]
+            L.hqa_solve_sub_tabu.restype = C.c_int
             L.hqa_run_trace.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i64, i32, u64,
                                         C.POINTER(RunOpts), vp, vp, vp, vp]
             L.hqa_run_trace.restype = C.c_int
@@ -368,6 +370,17 @@ class Context:
         out, e = out
         _check(lib().hqa_solve_sub(self._h, R, _ptr(spins), _ptr(frozen), int(n), _ptr(out),
                                    _ptr(e), _stream_ptr(stream)), "hqa_solve_sub")
+        return out, e
+
+    def solve_sub_tabu(self, spins, frozen, n, iters, tenure, stream=None):
+        """hqa_solve_sub_tabu: (spins [R][N], full energies [R]) of the tabu search."""
+        import torch
+        R = spins.shape[0]
+        out = torch.empty_like(spins)
+        e = torch.empty(R, dtype=torch.int64, device=spins.device)
+        _check(lib().hqa_solve_sub_tabu(self._h, R, _ptr(spins), _ptr(frozen), int(n), int(iters),
+                                        int(tenure), _ptr(out), _ptr(e), _stream_ptr(stream)),
+               "hqa_solve_sub_tabu")
         return out, e
 
     def solve_sub_noalloc(self, spins, frozen, n, out_spins, out_energy=None, stream=None):

@@ -1,0 +1,72 @@
+"""Tabu-search sub-solve on the GPU (ambivalent sets of 48 to 1024 spins, too large
+to enumerate) against the oracle's statement of the same deterministic search:
+spins and energies bit-exact.  On small sets it never beats the exact optimum and
+never returns worse than its input."""
+import numpy as np
+import pytest
+
+from paper_2004_03972_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hqa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2004_03972_gb300 import build, hqa as H
+    build.build()
+    return H
+
+
+@pytest.mark.parametrize("inst_name,n,iters,tenure", [
+    ("er800", 48, 480, 8), ("er800", 200, 2000, 20), ("er800", 1000, 4000, 20),
+    ("er_h", 120, 1200, 10), ("torus", 64, 640, 6)])
+def test_tabu_bit_exact(hqa, orc, inst_name, n, iters, tenure):
+    inst = {"er800": instances.er_pm1(800, 0.06, 1200),
+            "er_h": instances.with_integer_field(instances.er_pm1(300, 0.05, 5), 2, 9),
+            "torus": instances.torus_pm1(20, 15, 3)}[inst_name]
+    ctx = hqa.Context.from_instance(inst)
+    R = 4
+    out = ctx.run(600, R, seed=12, sched=hqa.schedule(n_ambivalent=n),
+                  outputs=("phibar", "spins", "frozen", "energy"))
+    ts, te = ctx.solve_sub_tabu(out["spins"], out["frozen"], n, iters, tenure)
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    s, f = out["spins"].cpu().numpy(), out["frozen"].cpu().numpy()
+    for r in range(R):
+        ws, we = orc.subsolve_tabu(pr, s[r], f[r], iters, tenure)
+        assert np.array_equal(ts[r].cpu().numpy(), ws), r
+        assert int(te[r]) == we
+    assert torch.all(te <= out["energy"])
+
+
+def test_tabu_against_exact_on_small_sets(hqa, orc):
+    inst = instances.er_pm1(800, 0.06, 1200)
+    ctx = hqa.Context.from_instance(inst)
+    R, n = 16, 16
+    out = ctx.run(600, R, seed=3, sched=hqa.schedule(n_ambivalent=n),
+                  outputs=("phibar", "spins", "frozen", "energy"))
+    ts, te = ctx.solve_sub_tabu(out["spins"], out["frozen"], n, 400, 4)
+    xs, xe = ctx.solve_sub(out["spins"], out["frozen"], n)
+    ctx.sync()
+    assert torch.all(te >= xe) and torch.all(te <= out["energy"])
+    assert (te == xe).float().mean().item() >= 0.5
+
+
+def test_tabu_rejects(hqa):
+    inst = instances.er_pm1(200, 0.05, 2)
+    ctx = hqa.Context.from_instance(inst)
+    s = torch.ones((2, inst.N), dtype=torch.int8, device="cuda")
+    f = torch.zeros((2, inst.N), dtype=torch.uint8, device="cuda")   # all 200 ambivalent
+    with pytest.raises(hqa.HQAError):
+        ctx.solve_sub_tabu(s, f, 2000, 10, 2)                        # n above 1024
+    o, _ = ctx.solve_sub_tabu(s, f, 100, 10, 2)                      # 200 ambivalent > n
+    with pytest.raises(hqa.HQAError):
+        ctx.sync()
+    assert torch.equal(o, s)
+    sg = hqa.Context.from_instance(instances.uniform_sg(64, 1))
+    s2 = torch.ones((1, 64), dtype=torch.int8, device="cuda")
+    with pytest.raises(hqa.HQAError):
+        sg.solve_sub_tabu(s2, torch.ones_like(s2, dtype=torch.uint8), 4, 10, 2)
