@@ -51,7 +51,7 @@ CONFIGS = {
                         "n=24 exact sub-solve, tcgen05 field",
                    R=4096, S=10000, n=24, kind="dense", sched="paper",
                    variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
-                   cpu_steps=200),
+                   cpu_steps=200, tabu=dict(n=1000, iters=10000, tenure=20, replicas=512)),
     "sg2000": dict(desc="uniform spin glass N=2000 (J ~ U[-1,1] fully connected, h ~ U[-2,2]), "
                         "4096 replicas, 10000 steps, paper schedule, tcgen05 field; quality = "
                         "FP64 Ising energy of the readout (no sub-solve: real couplings)",
@@ -440,6 +440,29 @@ def run_ours(args):
     roof["kernel_ms"] = 1e3 * t_md
     roof["plan"] = plan
 
+    tabu = None
+    if cfg.get("tabu"):
+        # large-n sub-solve (the paper's HQA(TS1000) shape): tabu search on the n least
+        # frozen spins of the headline run's readout, timed on its own with CUDA events
+        tb = cfg["tabu"]
+        Rt = tb["replicas"]
+        o2 = ctx.run(S, Rt, seed=seed_base, sched=hqa.schedule(n_ambivalent=tb["n"]),
+                     precision=hv["prec"], outputs=("phibar", "spins", "frozen", "energy"))
+        ts = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, te = ctx.solve_sub_tabu(o2["spins"], o2["frozen"], tb["n"], tb["iters"], tb["tenure"])
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        gain = (o2["energy"] - te).double()
+        tabu = {"n": tb["n"], "iters": tb["iters"], "tenure": tb["tenure"], "replicas": Rt,
+                "ms": float(np.median(ts)),
+                "flips_per_s": Rt * tb["iters"] / (float(np.median(ts)) / 1e3),
+                "median_energy_gain_over_readout": float(gain.median()),
+                "bound": "latency: one block-wide argmin and 4 barriers per flip"}
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
     # launches per pipeline step: MD (+ init and output copy on the dense path),
     # readout, energy, sub-solve (prep, enumeration, assemble, energy)
@@ -477,6 +500,8 @@ def run_ours(args):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if tabu:
+        line["tabu_sub_solve"] = tabu
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
