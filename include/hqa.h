@@ -463,6 +463,17 @@ hqa_status hqa_capture_end(void* stream, hqa_graph** out);
 hqa_status hqa_graph_launch(hqa_graph* graph, void* stream);
 void hqa_graph_destroy(hqa_graph* graph);
 
+/* Exercises the dense kernel's bounded waits (every spin of the persistent
+ * tensor-core MD kernel gives up after a time limit, latches
+ * HQA_ERR_TIMEOUT and leaves, so a lost arrival never hangs the GPU).
+ * Arms a one-shot check for the next dense MD launch on `ctx`: before step
+ * `step` every CTA's producer waits until the device word `flag` is
+ * nonzero, for at most limit_ns (1 ns .. 10 s).  With a flag that nothing
+ * sets the wait runs out, the launch stops early and hqa_sync returns
+ * HQA_ERR_TIMEOUT; the context stays usable.  With a set flag the launch
+ * is unchanged.  Dense contexts only (UNSUPPORTED otherwise). */
+hqa_status hqa_arm_wait_check(hqa_ctx* ctx, const uint32_t* flag, int64_t step, int64_t limit_ns);
+
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream);

@@ -307,6 +307,11 @@ struct DenseMDArgs {
     int64_t S;
     int W, N, Npad, Rpad, R, KT, Mt, M;
     int rep0;                // global index of this launch's first replica (random draws)
+    // armed check of the bounded-wait path (hqa_arm_wait_check): before step
+    // wait_step every producer waits for *wait_flag != 0, at most wait_ns
+    const unsigned int* wait_flag;
+    int64_t wait_step;
+    uint64_t wait_ns;
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
@@ -376,6 +381,17 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
             uint32_t it = 0;
             for (int64_t m = 0; m < a.S && !*abort; ++m) {
                 for (int hh = 0; hh < NPASS && !*abort; ++hh) {
+                    if (a.wait_flag && m == a.wait_step && hh == 0) {
+                        const uint64_t t0 = tc::globaltimer();
+                        uint32_t spins = 0;
+                        while (ld_acquire(a.wait_flag) == 0u) {
+                            if ((++spins & 63u) == 0 && tc::globaltimer() - t0 > a.wait_ns) {
+                                *abort = 1;
+                                break;
+                            }
+                        }
+                        if (*abort) break;
+                    }
                     if (m > 0) {
                         const unsigned int* g = a.gbar + 2 * nc + hh;
                         const unsigned int target = (unsigned int)(a.Mt * m);
@@ -898,6 +914,12 @@ static hqa_status dense_md_chunk(hqa_ctx* ctx, const StepCoef* d_sched, int64_t 
     a.Mt = Mt;
     a.M = M;
     a.rep0 = rep0;
+    if (ctx->wait_flag) {   // one-shot: the first chunk of the next launch
+        a.wait_flag = static_cast<const unsigned int*>(ctx->wait_flag);
+        a.wait_step = ctx->wait_step;
+        a.wait_ns = ctx->wait_ns;
+        ctx->wait_flag = nullptr;
+    }
     CUtensorMap tmB;
     if (!make_tmap_bf16(&tmB, a.phib, (uint64_t)2 * Rpad, (uint64_t)kseg * Npad, NH))
         return HQA_ERR_CUDA;
@@ -955,5 +977,18 @@ hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S,
                                       phibar_out ? phibar_out + o : nullptr, split, st);
         if (s != HQA_OK) return s;
     }
+    return HQA_OK;
+}
+
+extern "C" hqa_status hqa_arm_wait_check(hqa_ctx* ctx, const uint32_t* flag, int64_t step,
+                                         int64_t limit_ns)
+{
+    if (!ctx || !flag || step < 0 || limit_ns < 1 || limit_ns > 10000000000ll ||
+        ((uintptr_t)flag % 4))
+        return HQA_ERR_INVALID_ARG;
+    if (!ctx->dense_tc) return HQA_ERR_UNSUPPORTED;
+    ctx->wait_flag = flag;
+    ctx->wait_step = step;
+    ctx->wait_ns = (uint64_t)limit_ns;
     return HQA_OK;
 }

@@ -167,6 +167,10 @@ struct hqa_ctx {
     // to BF16 and d_Jcat the three-segment operand [J_hi | J_lo | J_hi] of the
     // split product J_hi Phi_hi + J_lo Phi_hi + J_hi Phi_lo
     bool dense_exact = false;
+    // hqa_arm_wait_check: consumed by the next dense MD launch
+    const void* wait_flag = nullptr;
+    int64_t wait_step = 0;
+    uint64_t wait_ns = 0;
     void* d_Jcat = nullptr;        // [Mpad][3 Mpad] BF16 (non-exact J only)
     CUtensorMap tmJ3;
 };

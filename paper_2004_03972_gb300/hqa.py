@@ -36,6 +36,7 @@ EXPORTS = (
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
     "hqa_autotune", "hqa_hmd", "hqa_energy_f64", "hqa_run_trace", "hqa_solve_sub_tabu",
+    "hqa_arm_wait_check",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -139,6 +140,8 @@ def lib() -> C.CDLL:
                                        C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
                                        C.POINTER(i32), vp]
             L.hqa_autotune.restype = C.c_int
+            L.hqa_arm_wait_check.argtypes = [vp, vp, i64, i64]
+            L.hqa_arm_wait_check.restype = C.c_int
             L.hqa_solve_sub_tabu.argtypes = [vp, i32, vp, vp, i32, i32, i32, vp, vp, vp]
             L.hqa_solve_sub_tabu.restype = C.c_int
             L.hqa_run_trace.argtypes = [vp, C.POINTER(Schedule), C.c_double, i64, i64, i32, u64,
@@ -371,6 +374,11 @@ class Context:
         _check(lib().hqa_solve_sub(self._h, R, _ptr(spins), _ptr(frozen), int(n), _ptr(out),
                                    _ptr(e), _stream_ptr(stream)), "hqa_solve_sub")
         return out, e
+
+    def arm_wait_check(self, flag, step, limit_ns):
+        """hqa_arm_wait_check: the next dense MD launch waits for flag[0] != 0 before `step`."""
+        _check(lib().hqa_arm_wait_check(self._h, _ptr(flag), int(step), int(limit_ns)),
+               "hqa_arm_wait_check")
 
     def solve_sub_tabu(self, spins, frozen, n, iters, tenure, stream=None):
         """hqa_solve_sub_tabu: (spins [R][N], full energies [R]) of the tabu search."""
