@@ -464,10 +464,11 @@ def run_ours(args):
                 "median_energy_gain_over_readout": float(gain.median()),
                 "bound": "latency: one block-wide argmin and 4 barriers per flip"}
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
-    # launches per pipeline step: MD (+ init and output copy on the dense path),
-    # readout, energy, sub-solve (prep, enumeration, assemble, energy)
+    # launches per pipeline step: MD (+ init and output copy per chunk on the dense
+    # path), readout, energy; the exact sub-solve adds prep, packed minimum, packed
+    # argmin, scalar walk (returns at once for packed replicas), assemble and energy
     launches = (3 * plan.get("chunks", 1) if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + \
-        (0 if batch or real else 4)
+        (0 if batch or real else 6)
     line = {
         "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_pipe / args.steps,
