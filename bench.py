@@ -462,7 +462,7 @@ def run_ours(args):
                 "ms": float(np.median(ts)),
                 "flips_per_s": Rt * tb["iters"] / (float(np.median(ts)) / 1e3),
                 "median_energy_gain_over_readout": float(gain.median()),
-                "bound": "latency: one block-wide argmin and 4 barriers per flip"}
+                "bound": "issue: two block-wide argmins and 2 barriers per flip, row loads from L2"}
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
     # launches per pipeline step: MD (+ init and output copy per chunk on the dense
     # path), readout, energy; the exact sub-solve adds prep, packed minimum, packed

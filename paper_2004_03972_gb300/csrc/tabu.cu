@@ -7,23 +7,32 @@
 //   (until[a] < it) or would give a new best (E + d_a < E_best), flip the
 //   smallest (d_a, a), even uphill; update its neighbours' fields; make it
 //   tabu until it + tenure; a strictly lower E becomes the best assignment.
-// One CTA per replica, one thread per ambivalent spin (n <= 1024): the
-// choice is a block-wide minimum of 64-bit keys ((d_a + 2^31) << 32 | a),
-// then one warp updates the winner's neighbours through a shared-memory map
-// spin -> position in the ambivalent list.
+// One CTA per replica; each of its 512 threads owns two positions q and
+// q + 512 of the ascending ambivalent list (n <= 1024), so four CTAs share an
+// SM.  Per flip: every thread forms the keys ((d_a + 2^31) << 32 | q << 1 |
+// [s_a < 0]) of its positions; warps reduce them and every warp reduces the
+// 16 warp minima itself, so all threads learn the winner, its energy change
+// and its old spin (the bit below the position, which never decides a tie).
+// The running and best energies are register copies kept identical in all
+// threads.  The whole block then walks the winner's CSR row (unique,
+// off-diagonal columns) and updates the neighbours' fields through a
+// shared-memory map spin -> position: two barriers per flip.
 #include "hqa_internal.cuh"
 
 namespace {
 
-constexpr int kTabuThreads = 1024;
-constexpr int kTabuMaxN = 1024;
+constexpr int kTabuThreads = 512;
+constexpr int kTabuPer = 2;
+constexpr int kTabuWarps = kTabuThreads / 32;
+constexpr int kTabuMaxN = kTabuThreads * kTabuPer;
 
 size_t tabu_smem(int N)
 {
-    return (((size_t)N * 2 + 15) & ~(size_t)15) + (size_t)kTabuMaxN * (4 + 4 + 4 + 1 + 1);
+    // pos int16[N]; amb, f, until, rb, re int32[max n]; s, bs int8[max n]
+    return (((size_t)N * 2 + 15) & ~(size_t)15) + (size_t)kTabuMaxN * (5 * 4 + 2);
 }
 
-__global__ void __launch_bounds__(kTabuThreads, 1) k_sub_tabu(
+__global__ void __launch_bounds__(kTabuThreads, 4) k_sub_tabu(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const int8_t* __restrict__ val, const int32_t* __restrict__ h, int N, int nmax,
     const int8_t* __restrict__ spins, const uint8_t* __restrict__ frozen, int iters, int tenure,
@@ -34,47 +43,48 @@ __global__ void __launch_bounds__(kTabuThreads, 1) k_sub_tabu(
     int32_t* amb = reinterpret_cast<int32_t*>(sm + (((size_t)N * 2 + 15) & ~(size_t)15));
     int32_t* f = amb + kTabuMaxN;
     int32_t* until = f + kTabuMaxN;
-    int8_t* s = reinterpret_cast<int8_t*>(until + kTabuMaxN);
+    int32_t* rb = until + kTabuMaxN;
+    int32_t* re = rb + kTabuMaxN;
+    int8_t* s = reinterpret_cast<int8_t*>(re + kTabuMaxN);
     int8_t* bs = s + kTabuMaxN;
-    __shared__ int cnt[kTabuThreads];
-    __shared__ int s_n;
-    __shared__ unsigned long long wmin[kTabuThreads / 32];
-    __shared__ unsigned long long s_win;
-    __shared__ long long s_rel, s_best;
-    __shared__ int s_improved;
+    __shared__ int wsum[kTabuWarps];
+    __shared__ unsigned long long wmin[kTabuWarps];
 
     const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int8_t* sin = spins + (size_t)r * N;
     const uint8_t* fr = frozen + (size_t)r * N;
     int8_t* so = out + (size_t)r * N;
 
-    // ambivalent list in ascending index: a contiguous chunk per thread, then a scan
-    const int per = (N + blockDim.x - 1) / blockDim.x;
-    const int lo = t * per, hi = min(N, lo + per);
+    // ambivalent list in ascending index: a contiguous chunk per thread, then a
+    // block-wide exclusive scan of the chunk counts (warp scans + warp totals)
+    const int per = (N + kTabuThreads - 1) / kTabuThreads;
+    const int lo = min(N, t * per), hi = min(N, lo + per);
     int c = 0;
     for (int i = lo; i < hi; ++i) c += fr[i] ? 0 : 1;
-    cnt[t] = c;
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    if (t == 0) {
-        int acc = 0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            const int v = cnt[k];
-            cnt[k] = acc;
-            acc += v;
+    if (warp == 0) {
+        int v = lane < kTabuWarps ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
         }
-        s_n = acc;
-        s_rel = 0;
-        s_best = 0;
+        if (lane < kTabuWarps) wsum[lane] = v;
     }
     __syncthreads();
-    const int n = s_n;
+    const int n = wsum[kTabuWarps - 1];
     if (n > nmax || n > kTabuMaxN) {
-        for (int i = t; i < N; i += blockDim.x) so[i] = sin[i];
+        for (int i = t; i < N; i += kTabuThreads) so[i] = sin[i];
         if (t == 0) atomicOr(status, HQA_DEV_BAD_SUBPROBLEM);
         return;
     }
     {
-        int k = cnt[t];
+        int k = (warp ? wsum[warp - 1] : 0) + x - c;
         for (int i = lo; i < hi; ++i) {
             if (fr[i]) {
                 pos[i] = -1;
@@ -85,24 +95,46 @@ __global__ void __launch_bounds__(kTabuThreads, 1) k_sub_tabu(
         }
     }
     __syncthreads();
-    if (t < n) {
-        const int a = amb[t];
-        int g = h ? h[a] : 0;
-        for (int k = row_ptr[a]; k < row_ptr[a + 1]; ++k)
-            if (col[k] != a) g += (int)val[k] * (int)sin[col[k]];
-        f[t] = g;
-        s[t] = sin[a];
-        bs[t] = sin[a];
-        until[t] = 0;
+    // fields f_a = h_a + sum_j J_aj s_j: one warp per position, lanes across the row
+    for (int q = warp; q < n; q += kTabuWarps) {
+        const int a = amb[q];
+        const int b = row_ptr[a], e = row_ptr[a + 1];
+        int g = 0;
+        for (int k = b + lane; k < e; k += 32) g += (int)val[k] * (int)sin[col[k]];
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        if (lane == 0) {
+            f[q] = g + (h ? h[a] : 0);
+            rb[q] = b;
+            re[q] = e;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kTabuPer; ++u) {
+        const int q = t + u * kTabuThreads;
+        if (q < n) {
+            s[q] = sin[amb[q]];
+            bs[q] = s[q];
+            until[q] = 0;
+        }
     }
     __syncthreads();
 
+    long long rel = 0, best = 0;   // energies relative to the input assignment
     for (int it = 1; it <= iters; ++it) {
         unsigned long long key = ~0ull;
-        if (t < n) {
-            const int d = -2 * (int)s[t] * f[t];
-            if (until[t] < it || s_rel + d < s_best)
-                key = ((unsigned long long)((uint32_t)d ^ 0x80000000u) << 32) | (uint32_t)t;
+#pragma unroll
+        for (int u = 0; u < kTabuPer; ++u) {
+            const int q = t + u * kTabuThreads;
+            if (q < n) {
+                const int sq = s[q];
+                const int d = -2 * sq * f[q];
+                if (until[q] < it || rel + d < best) {
+                    const unsigned long long kq =
+                        ((unsigned long long)((uint32_t)d ^ 0x80000000u) << 32) |
+                        ((uint32_t)q << 1) | (sq < 0 ? 1u : 0u);
+                    key = kq < key ? kq : key;
+                }
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, key, o);
@@ -110,43 +142,37 @@ __global__ void __launch_bounds__(kTabuThreads, 1) k_sub_tabu(
         }
         if (lane == 0) wmin[warp] = key;
         __syncthreads();
-        if (warp == 0) {
-            unsigned long long v = lane < (int)(blockDim.x >> 5) ? wmin[lane] : ~0ull;
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
-                v = u < v ? u : v;
+        unsigned long long win = lane < kTabuWarps ? wmin[lane] : ~0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, win, o);
+            win = v < win ? v : win;
+        }
+        if (win != ~0ull) {   // uniform: every spin tabu and none aspirates skips the flip
+            const uint32_t low = (uint32_t)win;
+            const int w = (int)(low >> 1);
+            const int sw = (low & 1u) ? 1 : -1;   // the winner's new spin
+            rel += (int)((uint32_t)(win >> 32) ^ 0x80000000u);
+            const bool improved = rel < best;
+            if (improved) best = rel;
+            if ((w & (kTabuThreads - 1)) == t) {
+                s[w] = (int8_t)sw;
+                until[w] = it + tenure;
             }
-            if (lane == 0) s_win = v;
-        }
-        __syncthreads();
-        const unsigned long long win = s_win;
-        if (win == ~0ull) continue;   // every spin tabu and none aspirates (uniform)
-        const int w = (int)(win & 0xffffffffull);
-        const int d = (int)((uint32_t)(win >> 32) ^ 0x80000000u);
-        if (t == w) {
-            s[w] = (int8_t)-s[w];
-            until[w] = it + tenure;
-        }
-        if (t == 0) s_rel += d;
-        __syncthreads();
-        if (warp == 0) {
-            const int a = amb[w];
-            const int sw = s[w];
-            for (int k = row_ptr[a] + lane; k < row_ptr[a + 1]; k += 32) {
-                const int j = col[k];
-                const int p = j != a ? pos[j] : -1;
+            for (int k = rb[w] + t; k < re[w]; k += kTabuThreads) {
+                const int p = pos[col[k]];
                 if (p >= 0) f[p] += 2 * (int)val[k] * sw;   // each neighbour once per row
             }
-            if (lane == 0) {
-                s_improved = s_rel < s_best ? 1 : 0;
-                if (s_improved) s_best = s_rel;
+            if (improved) {
+#pragma unroll
+                for (int u = 0; u < kTabuPer; ++u) {
+                    const int q = t + u * kTabuThreads;
+                    if (q < n) bs[q] = s[q];
+                }
             }
         }
         __syncthreads();
-        if (s_improved && t < n) bs[t] = s[t];
     }
-    __syncthreads();
-    for (int i = t; i < N; i += blockDim.x) so[i] = pos[i] >= 0 ? bs[pos[i]] : sin[i];
+    for (int i = t; i < N; i += kTabuThreads) so[i] = pos[i] >= 0 ? bs[pos[i]] : sin[i];
 }
 
 }  // namespace

@@ -1,7 +1,10 @@
-"""Tabu-search sub-solve on the GPU (ambivalent sets of 48 to 1024 spins, too large
+"""Tabu-search sub-solve on the GPU (ambivalent sets of 40 to 1024 spins, too large
 to enumerate) against the oracle's statement of the same deterministic search:
-spins and energies bit-exact.  On small sets it never beats the exact optimum and
-never returns worse than its input."""
+spins and energies bit-exact.  The cases span positions owned by both halves of the
+block (n > 512), the maximum n = 1024, dense rows (K2000: the block walks 1999
+neighbours per flip) and a tenure longer than the set, where every spin turns tabu
+and iterations without an aspirating candidate flip nothing.  On small sets it never
+beats the exact optimum and never returns worse than its input."""
 import numpy as np
 import pytest
 
@@ -22,11 +25,14 @@ def hqa():
 
 @pytest.mark.parametrize("inst_name,n,iters,tenure", [
     ("er800", 48, 480, 8), ("er800", 200, 2000, 20), ("er800", 1000, 4000, 20),
-    ("er_h", 120, 1200, 10), ("torus", 64, 640, 6)])
+    ("er_h", 120, 1200, 10), ("torus", 64, 640, 6), ("er800", 40, 400, 60),
+    ("torus40", 1024, 3000, 30), ("sk2000", 1000, 3000, 20)])
 def test_tabu_bit_exact(hqa, orc, inst_name, n, iters, tenure):
-    inst = {"er800": instances.er_pm1(800, 0.06, 1200),
-            "er_h": instances.with_integer_field(instances.er_pm1(300, 0.05, 5), 2, 9),
-            "torus": instances.torus_pm1(20, 15, 3)}[inst_name]
+    inst = {"er800": lambda: instances.er_pm1(800, 0.06, 1200),
+            "er_h": lambda: instances.with_integer_field(instances.er_pm1(300, 0.05, 5), 2, 9),
+            "torus": lambda: instances.torus_pm1(20, 15, 3),
+            "torus40": lambda: instances.torus_pm1(40, 40, 4),
+            "sk2000": lambda: instances.sk_pm1(2000, 1300)}[inst_name]()
     ctx = hqa.Context.from_instance(inst)
     R = 4
     out = ctx.run(600, R, seed=12, sched=hqa.schedule(n_ambivalent=n),
