@@ -10,6 +10,10 @@ Workloads (--config):
          Variants on the tcgen05 dense kernel: split BF16 operand (hi + lo,
          ~16 significant bits: the FP32-accurate reference variant) and plain
          BF16 operand.
+  sg2000, sg10000  uniform spin glass (J ~ U[-1, 1], h ~ U[-2, 2]) at N = 2000
+         (4096 replicas, 10000 steps) and N = 10000 (1024 replicas, 2000 steps)
+         on the dense kernel; quality is the FP64 energy of the readout.
+  uneven512  512 instances of uneven size in one persistent batch launch.
   sk100  SK N = 100, 1 replica, 1000 steps, linear-Gamma schedule (latency).
 One bench "step" is the whole pipeline over all replicas: MD, readout,
 int64 energy/cut and the exact sub-solve of the n least-frozen spins.
@@ -58,6 +62,12 @@ CONFIGS = {
                    R=4096, S=10000, n=24, kind="dense_sg", sched="paper",
                    variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
                    cpu_steps=200),
+    "sg10000": dict(desc="uniform spin glass N=10000 (J ~ U[-1,1] fully connected, h ~ U[-2,2]), "
+                         "1024 replicas, 2000 steps, paper schedule, tcgen05 field; quality = "
+                         "FP64 Ising energy of the readout (no sub-solve: real couplings)",
+                    R=1024, S=2000, n=24, kind="dense_sg", sched="paper",
+                    variants=(("bf16x2", "PREC_BF16X2"), ("bf16", "PREC_BF16")), plain="bf16x2",
+                    cpu_steps=50),
     "uneven512": dict(desc="512 instances, N uniform in [200,5000], half random 3-regular, half "
                            "2-D tori, +-1, 64 replicas each, 5000 steps, one persistent batch launch",
                       R=64, S=5000, n=24, kind="batch", sched="paper",
@@ -82,6 +92,8 @@ def make_instance(name):
         return instances.sk_pm1(100, 1100)
     if name == "sg2000":
         return instances.uniform_sg(2000, 1350)
+    if name == "sg10000":
+        return instances.uniform_sg(10000, 1360)
     if name == "uneven512":
         return instances.uneven_batch(512, 200, 5000, 1400)
     raise KeyError(name)

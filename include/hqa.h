@@ -240,9 +240,15 @@ hqa_status hqa_energy(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, int64
 
 /* Ising energy (Results Eq. (1)) for any real couplings and field:
  *   E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i
- * with J, h as given at create (FP32), every product and sum in FP64 and a
- * fixed reduction order (the same inputs give the same bits).  spins:
- * device [R][N] int8; energy: device [R] double.  Not for batch contexts. */
+ * with J, h as given at create (FP32).  J and h are rounded once onto a grid
+ * 2^-s chosen per context (max_i (sum_j |J_ij| + 2|h_i|) 2^s <= 2^61; each
+ * value moves by at most 2^-(s+1)); the sum on that grid is exact (64-bit row
+ * sums, a 128-bit total) and rounded to double once.  So the same inputs give
+ * the same bits under any schedule, and integer J, h give exactly the int64
+ * energy.  spins: device [R][N] int8; energy: device [R] double, 8-byte
+ * aligned.  Workspace owned by the context (INVALID_ARG for bad pointers,
+ * TOO_LARGE beyond 2^21 replicas per call, UNSUPPORTED for batch contexts
+ * or row sums of |J| beyond 2^61). */
 hqa_status hqa_energy_f64(hqa_ctx* ctx, int32_t replicas, const int8_t* spins, double* energy,
                           void* stream);
 

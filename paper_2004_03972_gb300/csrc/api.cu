@@ -100,7 +100,7 @@ void free_ctx_device(hqa_ctx* c)
     void* ptrs[] = {c->d_row_ptr, c->d_col,   c->d_val,    c->d_val_i8, c->d_h,
                     c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
                     c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat,
-                    c->d_tune,    c->d_diag,   c->d_Jcat};
+                    c->d_tune,    c->d_diag,   c->d_Jcat,  c->d_efx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }

@@ -137,6 +137,9 @@ struct hqa_ctx {
     size_t feat_cap = 0;
     void* d_diag = nullptr;         // H_MD diagnostic: local field
     size_t diag_cap = 0;
+    void* d_efx = nullptr;          // fixed-point energy: spin masks and partial sums
+    size_t efx_cap = 0;
+    int fx_shift = -1;              // its grid 2^-fx_shift (computed on first use)
     void* d_tune = nullptr;         // autotuner probe outputs
     size_t tune_cap = 0;
     // autotuned (kernel, replicas per block) per (replicas, precision); used by

@@ -142,34 +142,107 @@ __global__ void __launch_bounds__(kThreads) k_energy_csr(const int32_t* __restri
                  cut ? cut + r : nullptr);
 }
 
-// Ising energy in FP64 for real-valued couplings and fields (Results Eq. (1)):
-// one block per replica, E = sum_i s_i (h_i + 1/2 sum_j J_ij s_j), each row sum
-// and each thread's partial in FP64, then a fixed-shape reduction (warp
-// shuffles, warps in order), so the result does not depend on timing.
-__global__ void __launch_bounds__(kThreads) k_energy_f64(const int32_t* __restrict__ row_ptr,
-                                                         const int32_t* __restrict__ col,
-                                                         const float* __restrict__ val,
-                                                         const float* __restrict__ h, int N,
-                                                         const int8_t* __restrict__ spins,
-                                                         double* __restrict__ energy)
+// Ising energy for real-valued couplings and fields (Results Eq. (1)), exact up
+// to one rounding of J and h onto a fixed-point grid.  The context's shift s
+// makes max_i (sum_j |J_ij| + 2 |h_i|) 2^s <= 2^61; every J_ij and h_i is rounded
+// to the nearest multiple of 2^-s (J~, h~: integers), and per replica
+//   2^(s+1) E = sum_i s_i (2 h~_i + sum_{j != i} J~_ij s_j)
+// is summed exactly: int64 row sums, a 128-bit total, one rounding to double at
+// the end.  Integer sums do not depend on their order, so the result is the
+// same under any schedule, and integer J, h give the int64 energy exactly.
+// A warp holds 32 replicas (a lane each) and walks each row once: lane k loads
+// entry k of a 32-entry slice, converts it and fetches the 32-replica sign mask
+// of its column; the slice is then broadcast entry by entry.
+constexpr int kFxWarps = 8;
+
+__device__ __forceinline__ long long fx_round(float v, int s)
 {
-    const int r = blockIdx.x;
-    const int8_t* s = spins + (size_t)r * N;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double g = 0.0;
-        for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) g += (double)val[k] * (double)s[col[k]];
-        acc += (double)s[i] * (0.5 * g + (h ? (double)h[i] : 0.0));
+    const uint32_t u = __float_as_uint(v);
+    const int e = (int)((u >> 23) & 0xffu);
+    long long m = (long long)(u & 0x7fffffu);
+    int ex = -149;                       // subnormal: m 2^-149
+    if (e != 0) {
+        m |= 0x800000;
+        ex = e - 150;                    // v = m 2^(e - 150)
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ double sh[kThreads / 32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    const int sh = ex + s;
+    long long q;
+    if (sh >= 0) q = m << sh;            // |v| 2^s <= 2^61: no overflow
+    else if (sh > -40) q = (m + (1ll << (-sh - 1))) >> (-sh);   // nearest, ties away from 0
+    else q = 0;
+    return (u >> 31) ? -q : q;
+}
+
+// masks[g][j] bit r: spin j of replica 32 g + r is -1 (replicas past R: +1)
+__global__ void __launch_bounds__(kThreads) k_spin_masks(const int8_t* __restrict__ spins, int R,
+                                                         int N, uint32_t* __restrict__ masks)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
+    if (j >= N) return;
+    uint32_t m = 0;
+    for (int r = 0; r < 32 && g * 32 + r < R; ++r)
+        m |= (spins[(size_t)(g * 32 + r) * N + j] < 0 ? 1u : 0u) << r;
+    masks[(size_t)g * N + j] = m;
+}
+
+// Block (chunk c, replica group g): rows [c rows, +rows) of the 32 replicas of
+// group g; part[c][32 g + lane] = sum over those rows of s_i (2 h~_i + g~_i).
+__global__ void __launch_bounds__(kFxWarps * 32) k_energy_fx(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const float* __restrict__ val, const float* __restrict__ h, int N, int rows, int s,
+    const uint32_t* __restrict__ masks, __int128* __restrict__ part, int Rp)
+{
+    const int c = blockIdx.x, g = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t* mk = masks + (size_t)g * N;
+    const int i0 = c * rows, i1 = min(N, i0 + rows);
+    __int128 acc = 0;
+    for (int i = i0 + warp; i < i1; i += kFxWarps) {
+        const int b = row_ptr[i], e = row_ptr[i + 1];
+        long long T = 0, A = 0;          // row sum, and its part over this lane's -1 spins
+        for (int base = b; base < e; base += 32) {
+            const int k = base + lane;
+            long long q = 0;
+            uint32_t m = 0;
+            if (k < e) {
+                q = fx_round(val[k], s);
+                m = mk[col[k]];
+            }
+            T += q;
+            const int cnt = min(32, e - base);
+#pragma unroll 4
+            for (int kk = 0; kk < cnt; ++kk) {
+                const long long qk = __shfl_sync(0xffffffffu, q, kk);
+                const uint32_t mkk = __shfl_sync(0xffffffffu, m, kk);
+                if ((mkk >> lane) & 1u) A += qk;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) T += __shfl_xor_sync(0xffffffffu, T, o);
+        const long long x = T - 2 * A + (h ? 2 * fx_round(h[i], s) : 0);
+        acc += ((mk[i] >> lane) & 1u) ? -(__int128)x : (__int128)x;
+    }
+    __shared__ __int128 sh[kFxWarps][32];
+    sh[warp][lane] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        energy[r] = t;
+    if (warp == 0) {
+        __int128 t = 0;
+        for (int w = 0; w < kFxWarps; ++w) t += sh[w][lane];
+        part[(size_t)c * Rp + g * 32 + lane] = t;
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_energy_fx_final(const __int128* __restrict__ part,
+                                                              int chunks, int Rp, int R, int s,
+                                                              double* __restrict__ energy)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    __int128 t = 0;
+    for (int c = 0; c < chunks; ++c) t += part[(size_t)c * Rp + r];
+    const bool neg = t < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+    const double d = (double)(unsigned long long)(a >> 64) * 18446744073709551616.0 +
+                     (double)(unsigned long long)a;
+    energy[r] = ldexp(neg ? -d : d, -(s + 1));
 }
 
 // Batch of instances: block b is replica b % R of instance b / R; each
@@ -233,10 +306,42 @@ extern "C" hqa_status hqa_energy_f64(hqa_ctx* ctx, int32_t replicas, const int8_
     if (!ctx || replicas < 1 || !spins || !energy || ((uintptr_t)energy % 8))
         return HQA_ERR_INVALID_ARG;
     if (ctx->is_batch) return HQA_ERR_UNSUPPORTED;
+    const int N = ctx->N;
+    if (ctx->fx_shift < 0) {
+        // the grid: the largest row bound B = sum_j |J_ij| + 2 |h_i| gets B 2^s <= 2^61
+        double B = 0.0;
+        for (int i = 0; i < N; ++i) {
+            double b = ctx->has_h ? 2.0 * std::fabs((double)ctx->h[i]) : 0.0;
+            for (int64_t k = ctx->row_ptr[i]; k < ctx->row_ptr[i + 1]; ++k)
+                b += std::fabs((double)ctx->val[k]);
+            B = std::max(B, b);
+        }
+        ctx->fx_shift = B > 0.0 ? std::min(200, (int)std::floor(61.0 - std::log2(B))) : 0;
+        if (ctx->fx_shift < 0) return HQA_ERR_UNSUPPORTED;   // |J| sums beyond 2^61
+    }
+    const int s = ctx->fx_shift;
+    const int G = (replicas + 31) / 32, Rp = G * 32;
+    if (G > 65535) return HQA_ERR_TOO_LARGE;   // grid y
+    // about four blocks per SM over (row chunk, replica group)
+    const int want = std::max(1, 4 * ctx->sm_count / G);
+    const int chunks = std::min(want, (N + kFxWarps - 1) / kFxWarps);
+    const int rows = (N + chunks - 1) / chunks;
+    const int nchunks = (N + rows - 1) / rows;
+    const size_t mask_bytes = ((size_t)G * N * 4 + 255) & ~(size_t)255;
+    const size_t bytes = mask_bytes + (size_t)nchunks * Rp * sizeof(__int128);
+    hqa_status st = hqa_reserve(ctx, &ctx->d_efx, &ctx->efx_cap, bytes);
+    if (st != HQA_OK) return st;
     hqa_capture_touch(ctx);
-    k_energy_f64<<<replicas, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-        ctx->d_row_ptr, ctx->d_col, ctx->d_val, ctx->has_h ? ctx->d_h : nullptr, ctx->N, spins,
-        energy);
+    uint32_t* masks = static_cast<uint32_t*>(ctx->d_efx);
+    __int128* part = reinterpret_cast<__int128*>(static_cast<char*>(ctx->d_efx) + mask_bytes);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    k_spin_masks<<<dim3((N + kThreads - 1) / kThreads, G), kThreads, 0, cs>>>(spins, replicas, N,
+                                                                             masks);
+    k_energy_fx<<<dim3(nchunks, G), kFxWarps * 32, 0, cs>>>(ctx->d_row_ptr, ctx->d_col, ctx->d_val,
+                                                           ctx->has_h ? ctx->d_h : nullptr, N,
+                                                           rows, s, masks, part, Rp);
+    k_energy_fx_final<<<(replicas + kThreads - 1) / kThreads, kThreads, 0, cs>>>(
+        part, nchunks, Rp, replicas, s, energy);
     return hqa_capture_note(cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA);
 }
 

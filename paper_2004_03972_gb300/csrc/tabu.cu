@@ -16,7 +16,10 @@
 // The running and best energies are register copies kept identical in all
 // threads.  The whole block then walks the winner's CSR row (unique,
 // off-diagonal columns) and updates the neighbours' fields through a
-// shared-memory map spin -> position: two barriers per flip.
+// shared-memory map spin -> position: two barriers per flip.  When every
+// |f_a| < 2^19 (the host bounds it by |h_a| + deg_a for unit couplings) a key
+// fits 32 bits, ((d_a + 2^20) << 11 | q << 1 | [s_a < 0]), and both minima are
+// one redux.sync each instead of five 64-bit shuffle rounds.
 #include "hqa_internal.cuh"
 
 namespace {
@@ -32,6 +35,42 @@ size_t tabu_smem(int N)
     return (((size_t)N * 2 + 15) & ~(size_t)15) + (size_t)kTabuMaxN * (5 * 4 + 2);
 }
 
+// Keys of one candidate and of "no candidate": 64-bit, or 32-bit when narrow.
+template <bool NARROW>
+struct TabuKey;
+template <>
+struct TabuKey<false> {
+    using T = unsigned long long;
+    static constexpr T kNone = ~0ull;
+    __device__ static T make(int d, int q, int sq)
+    {
+        return ((T)((uint32_t)d ^ 0x80000000u) << 32) | ((uint32_t)q << 1) | (sq < 0 ? 1u : 0u);
+    }
+    __device__ static T warp_min(T k)
+    {
+        for (int o = 16; o > 0; o >>= 1) {
+            const T v = __shfl_xor_sync(0xffffffffu, k, o);
+            k = v < k ? v : k;
+        }
+        return k;
+    }
+    __device__ static int delta(T k) { return (int)((uint32_t)(k >> 32) ^ 0x80000000u); }
+    __device__ static uint32_t low(T k) { return (uint32_t)k; }
+};
+template <>
+struct TabuKey<true> {
+    using T = uint32_t;
+    static constexpr T kNone = ~0u;
+    __device__ static T make(int d, int q, int sq)
+    {
+        return ((uint32_t)(d + (1 << 20)) << 11) | ((uint32_t)q << 1) | (sq < 0 ? 1u : 0u);
+    }
+    __device__ static T warp_min(T k) { return __reduce_min_sync(0xffffffffu, k); }
+    __device__ static int delta(T k) { return (int)(k >> 11) - (1 << 20); }
+    __device__ static uint32_t low(T k) { return k & 0x7ffu; }
+};
+
+template <bool NARROW>
 __global__ void __launch_bounds__(kTabuThreads, 4) k_sub_tabu(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const int8_t* __restrict__ val, const int32_t* __restrict__ h, int N, int nmax,
@@ -47,8 +86,10 @@ __global__ void __launch_bounds__(kTabuThreads, 4) k_sub_tabu(
     int32_t* re = rb + kTabuMaxN;
     int8_t* s = reinterpret_cast<int8_t*>(re + kTabuMaxN);
     int8_t* bs = s + kTabuMaxN;
+    using K = TabuKey<NARROW>;
+    using key_t = typename K::T;
     __shared__ int wsum[kTabuWarps];
-    __shared__ unsigned long long wmin[kTabuWarps];
+    __shared__ key_t wmin[kTabuWarps];
 
     const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int8_t* sin = spins + (size_t)r * N;
@@ -121,37 +162,31 @@ __global__ void __launch_bounds__(kTabuThreads, 4) k_sub_tabu(
 
     long long rel = 0, best = 0;   // energies relative to the input assignment
     for (int it = 1; it <= iters; ++it) {
-        unsigned long long key = ~0ull;
+        // aspiration E + d < E_best as d < gap; |d| <= 2^22, so the clamp keeps the test exact
+        const long long gl = best - rel;
+        const int gap = gl < -(1ll << 31) + 1 ? INT_MIN + 1 : (int)gl;
+        key_t key = K::kNone;
 #pragma unroll
         for (int u = 0; u < kTabuPer; ++u) {
             const int q = t + u * kTabuThreads;
             if (q < n) {
                 const int sq = s[q];
                 const int d = -2 * sq * f[q];
-                if (until[q] < it || rel + d < best) {
-                    const unsigned long long kq =
-                        ((unsigned long long)((uint32_t)d ^ 0x80000000u) << 32) |
-                        ((uint32_t)q << 1) | (sq < 0 ? 1u : 0u);
+                if (until[q] < it || d < gap) {
+                    const key_t kq = K::make(d, q, sq);
                     key = kq < key ? kq : key;
                 }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, key, o);
-            key = v < key ? v : key;
-        }
+        key = K::warp_min(key);
         if (lane == 0) wmin[warp] = key;
         __syncthreads();
-        unsigned long long win = lane < kTabuWarps ? wmin[lane] : ~0ull;
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, win, o);
-            win = v < win ? v : win;
-        }
-        if (win != ~0ull) {   // uniform: every spin tabu and none aspirates skips the flip
-            const uint32_t low = (uint32_t)win;
+        const key_t win = K::warp_min(lane < kTabuWarps ? wmin[lane] : K::kNone);
+        if (win != K::kNone) {   // uniform: every spin tabu and none aspirates skips the flip
+            const uint32_t low = K::low(win);
             const int w = (int)(low >> 1);
             const int sw = (low & 1u) ? 1 : -1;   // the winner's new spin
-            rel += (int)((uint32_t)(win >> 32) ^ 0x80000000u);
+            rel += K::delta(win);
             const bool improved = rel < best;
             if (improved) best = rel;
             if ((w & (kTabuThreads - 1)) == t) {
@@ -190,13 +225,30 @@ extern "C" hqa_status hqa_solve_sub_tabu(hqa_ctx* ctx, int32_t replicas, const i
     if (n > kTabuMaxN) return HQA_ERR_TOO_LARGE;
     const size_t smem = tabu_smem(ctx->N);
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
+    // |f_a| <= |h_a| + deg_a (unit couplings); an integer context has |h| <= 2^20 and
+    // N <= 2^16, so fields and energy changes stay far inside int32.  32-bit keys
+    // need |f_a| < 2^19.
+    int64_t fmax = 0;
+    for (int i = 0; i < ctx->N; ++i) {
+        const int64_t hb = ctx->has_h ? (int64_t)std::fabs((double)ctx->h[i]) : 0;
+        fmax = std::max(fmax, hb + (ctx->row_ptr[i + 1] - ctx->row_ptr[i]));
+    }
+    const bool narrow = fmax < ((int64_t)1 << 19);
     hqa_capture_touch(ctx);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (hqa_smem_attr((const void*)k_sub_tabu, smem) != cudaSuccess) return HQA_ERR_CUDA;
-    k_sub_tabu<<<replicas, kTabuThreads, smem, st>>>(ctx->d_row_ptr, ctx->d_col, ctx->d_val_i8,
-                                                     ctx->has_h ? ctx->d_h_i32 : nullptr, ctx->N, n,
-                                                     spins, frozen, iters, tenure, out_spins,
-                                                     ctx->d_status);
+    const void* fn = narrow ? (const void*)k_sub_tabu<true> : (const void*)k_sub_tabu<false>;
+    if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
+    const int32_t* hp = ctx->has_h ? ctx->d_h_i32 : nullptr;
+    if (narrow)
+        k_sub_tabu<true><<<replicas, kTabuThreads, smem, st>>>(ctx->d_row_ptr, ctx->d_col,
+                                                               ctx->d_val_i8, hp, ctx->N, n, spins,
+                                                               frozen, iters, tenure, out_spins,
+                                                               ctx->d_status);
+    else
+        k_sub_tabu<false><<<replicas, kTabuThreads, smem, st>>>(ctx->d_row_ptr, ctx->d_col,
+                                                                ctx->d_val_i8, hp, ctx->N, n, spins,
+                                                                frozen, iters, tenure, out_spins,
+                                                                ctx->d_status);
     if (cudaGetLastError() != cudaSuccess) return HQA_ERR_CUDA;
     if (out_energy) return hqa_capture_note(hqa_launch_energy(ctx, replicas, out_spins, out_energy,
                                                               nullptr, st));

@@ -8,7 +8,19 @@ everything else in FP64, 100 steps, dt = 1e-4; bounds are about twice that):
   BF16X2  (J_hi phi_hi + J_lo phi_hi + J_hi phi_lo): 4e-6, 1.3e-5, 7e-5 of rounding,
           plus FP32 state arithmetic -> bounds 1e-4, 1e-4, 3e-4
   field   (BF16): e_i <= 2^-8 of the conditioning scale (two BF16 roundings)
-Energies are FP64: within 1e-12 of the oracle's on the scale sum |J_ij| + sum |h_i|."""
+Split-operand field: the tensor core's FP32 accumulation over K = 3 Mpad products
+adds to the splitting's rounding (emulated: 7e-7, 6e-7, 3e-7 of the conditioning
+scale at N = 1000, 2000, 10000).  Measured on the GPU: 1.2e-6, 1.6e-6, 2.8e-6 of that
+scale, growing with K, uniform over row tiles.  Bound: sqrt(K) 2^-24 + 2^-20
+(4.3e-6 at N = 1000, 1.1e-5 at N = 10000).
+At N = 10,000 (79 row tiles, one column group per replica chunk), 30 steps at
+dt = 1e-4: BF16 0.55 % (phi), 1.0 % (p) -> bound 2.5e-2.  BF16X2: a field error of
+1.1e-5 of the scale with one sign at every element and step (the worst case of the
+bound above) moves the states by 2.0e-3 (phi) and 3.3e-3 (p) -> bound 3.5e-3.
+Energies: J and h rounded once onto a grid 2^-s (max row bound 2^61), exact integer
+sums, one rounding to double: within 1e-12 of the oracle's FP64 sum on the scale
+sum |J_ij| + sum |h_i| (the grid error is at most nnz 2^-(s+1): ~1e-7 at N = 10,000
+against 2.5e-5), and the same bits whatever the replica grouping."""
 import numpy as np
 import pytest
 
@@ -67,6 +79,56 @@ def test_states_after_100_steps(hqa, orc, N, R, prec, tol):
         assert _close(out["phibar"][r].cpu().numpy(), opbar, tol, scale=np.max(np.abs(ophi)))
 
 
+@pytest.fixture(scope="module")
+def sg10k(hqa, orc):
+    """The largest spin-glass size of the paper's Fig. 7 sweep: instance, context and
+    the oracle's 30-step states of replicas 0 and 7."""
+    inst = instances.uniform_sg(10000, 10007)
+    pr = orc.Problem.from_instance(inst)
+    ref = {r: orc.md_run(pr, 30, dt=1e-4, p0=orc.initial_momenta(21, r, inst.N)) for r in (0, 7)}
+    return hqa.Context.from_instance(inst), ref, inst
+
+
+@pytest.mark.parametrize("N", [1000, 10000])
+def test_split_field(hqa, sg10k, N):
+    """The BF16X2 field on the tensor cores, recovered from one leapfrog step from a
+    given phi(0) with p(0) = 0: p(1/2) = -F(phi(0), 0) / 2 (Methods, "Leapfrog
+    algorithm"), so L = (-2 p(1/2) - alpha M phi^(M-1)) / beta - 2 h |phi|."""
+    from oracle import oracle as orc
+    if N == 10000:
+        ctx, _, inst = sg10k
+    else:
+        inst = instances.uniform_sg(N, 7 + N)
+        ctx = hqa.Context.from_instance(inst)
+    R = 16
+    phi0 = np.random.default_rng(5).uniform(-1.5, 1.5, size=(R, N)).astype(np.float32)
+    out = ctx.run(1, R, seed=0, dt=1e-4, precision=hqa.PREC_BF16X2, kernel=hqa.KERNEL_DENSE,
+                  init=hqa.INIT_GIVEN, phi0=torch.from_numpy(phi0).cuda(),
+                  p0=torch.zeros((R, N), dtype=torch.float32, device="cuda"), outputs=("p",))
+    ctx.sync()
+    a0, b0 = orc.schedule(0.0)
+    x = phi0.astype(np.float64)
+    L = (-2 * out["p"].cpu().numpy().astype(np.float64) - a0 * 6 * x ** 5) / b0 \
+        - 2 * inst.h * np.abs(x)
+    ref = x @ inst.dense.T
+    scale = np.abs(x) @ np.abs(inst.dense).T + 2 * np.abs(inst.h) * np.abs(x)
+    K = 3 * ((N + 127) // 128 * 128)
+    assert np.max(np.abs(L - ref) / scale) <= np.sqrt(K) * 2.0 ** -24 + 2.0 ** -20
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 3.5e-3), (1, 2.5e-2)])
+def test_states_n10000(hqa, sg10k, prec, tol):
+    ctx, ref, _ = sg10k
+    assert ctx.plan(8, precision=prec)["kernel"] == hqa.KERNEL_DENSE
+    out = ctx.run(30, 8, seed=21, dt=1e-4, precision=prec, kernel=hqa.KERNEL_DENSE,
+                  outputs=("phi", "p", "phibar"))
+    ctx.sync()
+    for r, (ophi, op, opbar) in ref.items():
+        assert _close(out["phi"][r].cpu().numpy(), ophi, tol)
+        assert _close(out["p"][r].cpu().numpy(), op, tol, scale=1.0)
+        assert _close(out["phibar"][r].cpu().numpy(), opbar, tol, scale=np.max(np.abs(ophi)))
+
+
 def test_energy_f64(hqa, orc):
     inst = instances.uniform_sg(500, 9)
     ctx = hqa.Context.from_instance(inst)
@@ -78,13 +140,27 @@ def test_energy_f64(hqa, orc):
     for spins in (out["spins"], rand):
         e = ctx.energy_f64(spins).cpu().numpy()
         e2 = ctx.energy_f64(spins).cpu().numpy()
-        assert np.array_equal(e, e2)                      # fixed reduction order
+        assert np.array_equal(e, e2)                      # deterministic
         s = spins.cpu().numpy()
         for r in range(16):
             assert abs(e[r] - orc.energy_f64(pr, s[r])) <= 1e-12 * scale
     # the readout of the run is better than random configurations
     assert np.median(ctx.energy_f64(out["spins"]).cpu().numpy()) < np.median(
         ctx.energy_f64(rand).cpu().numpy())
+
+
+def test_energy_f64_n10000_and_grouping(hqa, orc, sg10k):
+    ctx, _, inst = sg10k
+    rng = np.random.default_rng(8)
+    s = torch.from_numpy(rng.choice(np.array([-1, 1], np.int8), size=(70, inst.N))).cuda()
+    e70 = ctx.energy_f64(s).cpu().numpy()
+    e1 = ctx.energy_f64(s[37:38].contiguous()).cpu().numpy()
+    assert e1[0] == e70[37]                               # exact sums: grouping-independent
+    pr = orc.Problem.from_instance(inst)
+    scale = np.abs(np.triu(inst.dense, 1)).sum() + np.abs(inst.h).sum()
+    sc = s.cpu().numpy()
+    for r in (0, 37, 69):
+        assert abs(e70[r] - orc.energy_f64(pr, sc[r])) <= 1e-12 * scale
 
 
 def test_energy_f64_equals_integer_energy(hqa):

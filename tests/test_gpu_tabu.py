@@ -48,6 +48,28 @@ def test_tabu_bit_exact(hqa, orc, inst_name, n, iters, tenure):
     assert torch.all(te <= out["energy"])
 
 
+@pytest.mark.parametrize("hmax", [3, 600000])
+def test_tabu_bit_exact_given_configurations(hqa, orc, hmax):
+    """Random spins and masks (no MD run).  Fields up to 600,000 exceed 2^19, so the
+    search takes its 64-bit keys; small fields take the 32-bit keys."""
+    inst = instances.with_integer_field(instances.er_pm1(500, 0.04, 8), hmax, 10)
+    ctx = hqa.Context.from_instance(inst)
+    rng = np.random.default_rng(hmax)
+    R, n = 6, 700 if hmax > 3 else 300
+    s = rng.choice(np.array([-1, 1], np.int8), size=(R, inst.N))
+    f = np.ones((R, inst.N), np.uint8)
+    for r in range(R):
+        f[r, rng.permutation(inst.N)[:min(n, inst.N) - r]] = 0
+    ts, te = ctx.solve_sub_tabu(torch.from_numpy(s).cuda(), torch.from_numpy(f).cuda(),
+                                min(n, inst.N), 1500, 12)
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    for r in range(R):
+        ws, we = orc.subsolve_tabu(pr, s[r], f[r], 1500, 12)
+        assert np.array_equal(ts[r].cpu().numpy(), ws), r
+        assert int(te[r]) == we
+
+
 def test_tabu_against_exact_on_small_sets(hqa, orc):
     inst = instances.er_pm1(800, 0.06, 1200)
     ctx = hqa.Context.from_instance(inst)
