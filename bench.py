@@ -391,8 +391,11 @@ def run_ours(args):
                 host_spins.copy_(out["spins"], non_blocking=True)
                 host_f.copy_(e, non_blocking=True)
                 return
-            if batch:   # seeds drive the batch's initial state: H2D of the run parameters only
-                ctx.run(S, R, seed=seed_base + 11 * k, sched=sched, precision=best_prec, out=out)
+            if batch:   # initial state in the batch layout ([R][N_k] blocks of every member)
+                d_p0.copy_(pin_p0, non_blocking=True)
+                d_phi0.copy_(pin_phi0, non_blocking=True)
+                ctx.run(S, R, sched=sched, precision=best_prec, init=hqa.INIT_GIVEN, phi0=d_phi0,
+                        p0=d_p0, out=out)
                 host_spins.copy_(out["spins"], non_blocking=True)
                 host_e.copy_(out["energy"], non_blocking=True)
                 host_c.copy_(out["cut"], non_blocking=True)
@@ -422,8 +425,9 @@ def run_ours(args):
     if batch:
         rb = hv["tuned"]["replicas_per_block"] if hv["tuned"] else 0
         plan = {"kernel": hqa.KERNEL_SCALAR, "replicas_per_block": rb, "members": count,
-                "note": "persistent batch kernel, replica blocking by the autotuner"}
-        kname = f"k_sparse_md_batch<{rb},{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
+                "note": "persistent batch kernel, replica blocking by the autotuner"
+                        if rb else "persistent batch kernel, the library's default blocking"}
+        kname = f"k_sparse_md_batch<{rb or '*'},{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
     else:
         plan = ctx.plan(R, precision=hv["prec"])
         kname = kernel_name(hqa, plan, hv["prec_name"])
@@ -505,7 +509,7 @@ def run_ours(args):
         "equal_cut": {"rule": "95% bootstrap interval of median(variant cut) - median(plain cut) "
                               "reaches 0", "plain": cfg["plain"]},
         "e2e": {"value": e2e_value, "unit": "spin-updates/s",
-                "h2d_bytes_per_step": 0 if batch else 2 * R * N * 4,
+                "h2d_bytes_per_step": 2 * R * N * 4,
                 "d2h_bytes_per_step": R * N + (1 if real else 2) * RR * 8},
         "gpu_launches": launches * args.steps,
         "roofline": roof,

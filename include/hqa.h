@@ -104,8 +104,8 @@ enum {
 typedef struct {
     int32_t precision;          /* HQA_PREC_*; default FP32 */
     int32_t init;               /* HQA_INIT_*; default PAPER */
-    const float* phi0;          /* device [R][N]; HQA_INIT_GIVEN only */
-    const float* p0;            /* device [R][N]; HQA_INIT_GIVEN only */
+    const float* phi0;          /* device [R][N] (a batch: its array layout); HQA_INIT_GIVEN only */
+    const float* p0;            /* device [R][N] (a batch: its array layout); HQA_INIT_GIVEN only */
     int32_t replicas_per_block; /* 0 = chosen by the library; else 1,2,4,8,16,32 */
     int32_t kernel;             /* HQA_KERNEL_*; default AUTO */
     int64_t start_step;         /* resume: first step index m0 (default 0).  With m0 > 0 the
@@ -177,7 +177,9 @@ hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const 
  * persistent launch (work items = member x replica block, longest first).
  * Batch array layout: member k's [R][N_k] block starts at R * (N_0 + ... +
  * N_{k-1}); per-replica results (energy, cut, tally) are [count][R].  Member
- * k draws its momenta from the stream seed + (k + 1) * 0x632BE59BD9B4E019.
+ * k draws its momenta from the stream seed + (k + 1) * 0x632BE59BD9B4E019
+ * (HQA_INIT_PAPER / RANDOM_FLUX) or takes phi0 / p0 in the same layout
+ * (HQA_INIT_GIVEN, which also resumes a batch with start_step).
  * Members need couplings in {-1, 0, +1}; hqa_readout and hqa_energy accept a
  * batch with the same layout; other calls return HQA_ERR_UNSUPPORTED.
  * Errors: INVALID_ARG (count < 1, null or batch member), UNSUPPORTED, OOM, CUDA. */

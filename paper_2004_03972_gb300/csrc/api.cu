@@ -313,12 +313,14 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     else hqa_run_opts_default(&o);
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    if (o.init == HQA_INIT_GIVEN || o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR ||
-        o.precision == HQA_PREC_BF16X2)
+    if (o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR || o.precision == HQA_PREC_BF16X2)
         return HQA_ERR_UNSUPPORTED;
-    if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_RANDOM_FLUX) return HQA_ERR_INVALID_ARG;
+    if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_GIVEN) return HQA_ERR_INVALID_ARG;
+    if (o.init == HQA_INIT_GIVEN && (!o.phi0 || !o.p0)) return HQA_ERR_INVALID_ARG;
+    if (o.start_step < 0 || (o.start_step > 0 && o.init != HQA_INIT_GIVEN)) return HQA_ERR_INVALID_ARG;
     if (misaligned(out->phi, 4) || misaligned(out->p, 4) || misaligned(out->phibar, 4) ||
-        misaligned(out->energy, 8) || misaligned(out->cut, 8) || misaligned(out->tally, 4))
+        misaligned(out->energy, 8) || misaligned(out->cut, 8) || misaligned(out->tally, 4) ||
+        misaligned(o.phi0, 4) || misaligned(o.p0, 4))
         return HQA_ERR_INVALID_ARG;
     const bool want_readout = out->spins || out->frozen || out->tally || out->energy || out->cut;
     const bool want_energy = out->energy || out->cut;
@@ -340,7 +342,7 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
         }
         if (RB == 0) return HQA_ERR_TOO_LARGE;
     }
-    s = upload_schedule(ctx, sched, dt, steps);
+    s = upload_schedule(ctx, sched, dt, steps, o.start_step);
     if (s != HQA_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t RN = (size_t)replicas * (size_t)ctx->total_spins;
@@ -360,7 +362,9 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     int8_t* spins = out->spins;
     if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
     s = hqa_batch_launch_md(ctx, RB, o.precision, ctx->d_sched, steps, sched->window, replicas,
-                            seed, o.init, sched->M, out->phi, out->p, phibar, st);
+                            seed, o.init, o.init == HQA_INIT_GIVEN ? o.phi0 : nullptr,
+                            o.init == HQA_INIT_GIVEN ? o.p0 : nullptr, sched->M, out->phi, out->p,
+                            phibar, st);
     if (s != HQA_OK) return s;
     if (want_readout) {
         s = hqa_launch_readout_batch(ctx, replicas, phibar, sched->n_ambivalent, spins, out->frozen,

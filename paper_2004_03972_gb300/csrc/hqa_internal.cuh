@@ -213,8 +213,9 @@ hqa_status hqa_vec_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t R,
 // sparse_md.cu
 hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out);
 hqa_status hqa_batch_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef* d_sched,
-                               int64_t S, int32_t W, int32_t R, uint64_t seed, int init, int M,
-                               float* phi_out, float* p_out, float* phibar_out, cudaStream_t st);
+                               int64_t S, int32_t W, int32_t R, uint64_t seed, int init,
+                               const float* phi0, const float* p0, int M, float* phi_out,
+                               float* p_out, float* phibar_out, cudaStream_t st);
 int hqa_sparse_pick_rb(const hqa_ctx* ctx, int32_t R, int prec);
 size_t hqa_sparse_smem_bytes(const hqa_ctx* ctx, int RB, int prec);
 hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const StepCoef* d_sched,

@@ -642,8 +642,9 @@ static cudaError_t launch_batch_t(const MDArgs* insts, const BatchItem* items, i
 }
 
 hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_sched, int64_t S,
-                               int32_t W, int32_t R, uint64_t seed, int init, int M,
-                               float* phi_out, float* p_out, float* phibar_out, cudaStream_t st)
+                               int32_t W, int32_t R, uint64_t seed, int init, const float* phi0,
+                               const float* p0, int M, float* phi_out, float* p_out,
+                               float* phibar_out, cudaStream_t st)
 {
     const int count = (int)b->members.size();
     const bool bf = prec == HQA_PREC_BF16;
@@ -676,6 +677,8 @@ hqa_status hqa_batch_launch_md(hqa_ctx* b, int RB, int prec, const StepCoef* d_s
         a.sched = d_sched;
         a.h = m->has_h ? m->d_h : nullptr;
         const size_t off = (size_t)R * (size_t)b->member_off[k];
+        a.phi0 = phi0 ? phi0 + off : nullptr;   // HQA_INIT_GIVEN: the same member blocks
+        a.p0 = p0 ? p0 + off : nullptr;
         a.phi_out = phi_out ? phi_out + off : nullptr;
         a.p_out = p_out ? p_out + off : nullptr;
         a.phibar_out = phibar_out ? phibar_out + off : nullptr;

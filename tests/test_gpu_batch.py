@@ -55,6 +55,39 @@ def test_batch_equals_member_runs_bitwise(hqa, rb):
         assert torch.equal(out["tally"][k * R:(k + 1) * R], alone["tally"])
 
 
+def test_batch_given_state_and_resume_bitwise(hqa):
+    """HQA_INIT_GIVEN on a batch takes phi0 / p0 in the batch layout: every member
+    equals its own run from its block, and a run split at step S1 (state handed over,
+    start_step = S1) reproduces the whole run bitwise."""
+    insts = _members()
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, S1, dt = 5, 200, 80, 1 / 400
+    sched = hqa.schedule(n_ambivalent=6)
+    tot = sum(i.N for i in insts)
+    g = torch.Generator().manual_seed(3)
+    phi0 = ((torch.rand((R, tot), generator=g) - 0.5) * 0.2).cuda()
+    p0 = (torch.randint(0, 2, (R, tot), generator=g) * 2 - 1).float().cuda()
+    kw = dict(sched=sched, dt=dt, init=hqa.INIT_GIVEN, replicas_per_block=2,
+              kernel=hqa.KERNEL_SCALAR)
+    out = batch.run(S, R, phi0=phi0, p0=p0, **kw)
+    batch.sync()
+    keys = ("phi", "p", "phibar", "spins")
+    views = {k: batch.split(out[k], R) for k in keys}
+    ph_b, p_b = batch.split(phi0, R), batch.split(p0, R)
+    for k, c in enumerate(ctxs):
+        alone = c.run(S, R, phi0=ph_b[k].contiguous(), p0=p_b[k].contiguous(), **kw)
+        c.sync()
+        for key in keys:
+            assert torch.equal(views[key][k], alone[key]), (k, key)
+    a = batch.run(S1, R, phi0=phi0, p0=p0, outputs=("phi", "p"), **kw)
+    b = batch.run(S - S1, R, phi0=a["phi"], p0=a["p"], start_step=S1,
+                  outputs=("phi", "p", "phibar"), **kw)
+    batch.sync()
+    for key in ("phi", "p", "phibar"):   # the window (100 steps) lies in the second call
+        assert torch.equal(b[key], out[key]), key
+
+
 def test_batch_matches_oracle(hqa, orc):
     insts = _members()
     ctxs = [hqa.Context.from_instance(i) for i in insts]
