@@ -424,10 +424,13 @@ def run_ours(args):
     hv = variants[head]
     if batch:
         rb = hv["tuned"]["replicas_per_block"] if hv["tuned"] else 0
-        plan = {"kernel": hqa.KERNEL_SCALAR, "replicas_per_block": rb, "members": count,
-                "note": "persistent batch kernel, replica blocking by the autotuner"
-                        if rb else "persistent batch kernel, the library's default blocking"}
-        kname = f"k_sparse_md_batch<{rb or '*'},{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
+        kb = hv["tuned"]["kernel"] if hv["tuned"] else hqa.KERNEL_AUTO
+        plan = {"kernel": kb, "replicas_per_block": rb, "members": count,
+                "note": "persistent batch kernel and replica blocking picked by the autotuner"
+                        if rb else "persistent batch kernel and blocking picked by the library"}
+        base = {hqa.KERNEL_LOWDEG: "k_batch_lowdeg", hqa.KERNEL_SCALAR: "k_sparse_md_batch"}.get(
+            kb, "k_batch_lowdeg|k_sparse_md_batch")
+        kname = f"{base}<{rb or '*'},{'true' if hv['prec_name'] == 'PREC_BF16' else 'false'}>"
     else:
         plan = ctx.plan(R, precision=hv["prec"])
         kname = kernel_name(hqa, plan, hv["prec_name"])

@@ -91,14 +91,18 @@ enum {
                            significant bits), two MMAs per k-step, FP32 accumulate */
 };
 
-/* Sparse kernel variants (both compute the same sums, in different orders). */
+/* Sparse kernel variants (all compute the same sums, in different orders). */
 enum {
     HQA_KERNEL_AUTO = 0,   /* vectorised when the blocking allows, else scalar */
     HQA_KERNEL_SCALAR = 1, /* one replica per lane, neighbour lists streamed from L1/L2 */
     HQA_KERNEL_VECTOR = 2, /* 16-byte gathers per lane, lists in shared memory; needs
                               replicas_per_block >= 4 (FP32) or >= 8 (BF16) */
-    HQA_KERNEL_DENSE = 3   /* tcgen05 tensor-core GEMM; dense contexts whose couplings
+    HQA_KERNEL_DENSE = 3,  /* tcgen05 tensor-core GEMM; dense contexts whose couplings
                               are exact in BF16, BF16 operand only */
+    HQA_KERNEL_LOWDEG = 4  /* batch contexts whose members have at most 4 couplings per
+                              spin and fewer than 2^15 spins: compact lists, operand and
+                              state of a work item all in shared memory; replicas_per_block
+                              1, 2 or 4.  AUTO picks it for such batches */
 };
 
 typedef struct {

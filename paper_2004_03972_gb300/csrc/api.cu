@@ -100,7 +100,8 @@ void free_ctx_device(hqa_ctx* c)
     void* ptrs[] = {c->d_row_ptr, c->d_col,   c->d_val,    c->d_val_i8, c->d_h,
                     c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
                     c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat,
-                    c->d_tune,    c->d_diag,   c->d_Jcat,  c->d_efx};
+                    c->d_tune,    c->d_diag,   c->d_Jcat,  c->d_efx,   c->d_ld,
+                    c->d_ldwork};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -263,7 +264,7 @@ hqa_status check_opts(const hqa_run_opts& o)
     const int rbq = o.replicas_per_block;
     if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
         return HQA_ERR_INVALID_ARG;
-    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_DENSE) return HQA_ERR_INVALID_ARG;
+    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_LOWDEG) return HQA_ERR_INVALID_ARG;
     return HQA_OK;
 }
 
@@ -271,6 +272,7 @@ hqa_status check_opts(const hqa_run_opts& o)
 // blocking allows it and its shared-memory image fits, else the scalar one.
 hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& opts, const SparsePlan** plan)
 {
+    if (opts.kernel == HQA_KERNEL_LOWDEG) return HQA_ERR_UNSUPPORTED;   // batch contexts only
     hqa_run_opts o = opts;
     if (o.kernel == HQA_KERNEL_AUTO && o.replicas_per_block == 0) {
         const auto it = ctx->tuned.find({R, o.precision});
@@ -302,8 +304,10 @@ hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& opts, const 
 }
 
 // Batch run: one persistent launch over (member, replica block) items, then
-// batched readout and energy.  Replica blocking: the largest RB whose
-// operand buffers fit every member and that leaves at least two items per SM.
+// batched readout and energy.  Kernel: the low-degree one when every member
+// allows it (lists on chip), else the list-streaming one.  Replica blocking:
+// the largest RB whose shared-memory image fits every member and that leaves
+// at least two items per SM.
 hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t steps,
                      int32_t replicas, uint64_t seed, const hqa_run_opts* opts,
                      const hqa_result* out, void* stream)
@@ -315,6 +319,23 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     if (s != HQA_OK) return s;
     if (o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR || o.precision == HQA_PREC_BF16X2)
         return HQA_ERR_UNSUPPORTED;
+    // kernel and blocking: the caller's, else the autotuned pair, else the
+    // low-degree kernel when every member allows it, else the list-streaming one
+    int kern = o.kernel;
+    int RB = o.replicas_per_block;
+    if (kern == HQA_KERNEL_AUTO && RB == 0) {
+        const auto it = ctx->tuned.find({replicas, o.precision});
+        if (it != ctx->tuned.end()) {
+            kern = it->second.first;
+            RB = it->second.second;
+        }
+    }
+    if (kern == HQA_KERNEL_AUTO) kern = hqa_lowdeg_eligible(ctx) ? HQA_KERNEL_LOWDEG : HQA_KERNEL_SCALAR;
+    if (kern == HQA_KERNEL_LOWDEG) {
+        if (!hqa_lowdeg_eligible(ctx)) return HQA_ERR_UNSUPPORTED;
+        if (RB == 0) RB = hqa_lowdeg_pick_rb(ctx, replicas, o.precision);
+        if (RB == 0) return HQA_ERR_TOO_LARGE;
+    }
     if (o.init < HQA_INIT_PAPER || o.init > HQA_INIT_GIVEN) return HQA_ERR_INVALID_ARG;
     if (o.init == HQA_INIT_GIVEN && (!o.phi0 || !o.p0)) return HQA_ERR_INVALID_ARG;
     if (o.start_step < 0 || (o.start_step > 0 && o.init != HQA_INIT_GIVEN)) return HQA_ERR_INVALID_ARG;
@@ -325,11 +346,6 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     const bool want_readout = out->spins || out->frozen || out->tally || out->energy || out->cut;
     const bool want_energy = out->energy || out->cut;
     if (want_energy && !ctx->integer) return HQA_ERR_UNSUPPORTED;
-    int RB = o.replicas_per_block;
-    if (RB == 0) {
-        const auto it = ctx->tuned.find({replicas, o.precision});
-        if (it != ctx->tuned.end()) RB = it->second.second;
-    }
     if (RB == 0) {
         const int cands[6] = {32, 16, 8, 4, 2, 1};
         for (int rb : cands) {
@@ -361,10 +377,14 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     }
     int8_t* spins = out->spins;
     if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
-    s = hqa_batch_launch_md(ctx, RB, o.precision, ctx->d_sched, steps, sched->window, replicas,
-                            seed, o.init, o.init == HQA_INIT_GIVEN ? o.phi0 : nullptr,
-                            o.init == HQA_INIT_GIVEN ? o.p0 : nullptr, sched->M, out->phi, out->p,
-                            phibar, st);
+    const float* phi0 = o.init == HQA_INIT_GIVEN ? o.phi0 : nullptr;
+    const float* p0 = o.init == HQA_INIT_GIVEN ? o.p0 : nullptr;
+    if (kern == HQA_KERNEL_LOWDEG)
+        s = hqa_lowdeg_launch_md(ctx, RB, o.precision, ctx->d_sched, steps, sched->window, replicas,
+                                 seed, o.init, phi0, p0, sched->M, out->phi, out->p, phibar, st);
+    else
+        s = hqa_batch_launch_md(ctx, RB, o.precision, ctx->d_sched, steps, sched->window, replicas,
+                                seed, o.init, phi0, p0, sched->M, out->phi, out->p, phibar, st);
     if (s != HQA_OK) return s;
     if (want_readout) {
         s = hqa_launch_readout_batch(ctx, replicas, phibar, sched->n_ambivalent, spins, out->frozen,
@@ -589,6 +609,7 @@ static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // dense tensor-core path: dense contexts exact in BF16, BF16 operand
     const bool tc_prec = o.precision == HQA_PREC_BF16 || o.precision == HQA_PREC_BF16X2;
+    if (o.kernel == HQA_KERNEL_LOWDEG) return HQA_ERR_UNSUPPORTED;   // batch contexts only
     const bool dense = o.kernel == HQA_KERNEL_DENSE ||
                        (o.kernel == HQA_KERNEL_AUTO && tc_prec && hqa_dense_md_possible(ctx, replicas));
     if (dense && (!ctx->dense_tc || !tc_prec)) return HQA_ERR_UNSUPPORTED;

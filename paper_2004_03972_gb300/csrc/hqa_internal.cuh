@@ -156,6 +156,15 @@ struct hqa_ctx {
     void* d_bwork = nullptr;        // per-run instance arguments, work items, queue counter
     size_t bwork_cap = 0;
     std::vector<char> bwork_host;   // what d_bwork holds (tables are uploaded only on change)
+    // low-degree batch kernel: eligibility (0 unknown, 1 yes, -1 no), the members'
+    // compact lists (built once) and per-run tables
+    int ld_state = 0;
+    void* d_ld = nullptr;
+    size_t ld_cap = 0;
+    std::vector<int64_t> ld_off;
+    void* d_ldwork = nullptr;
+    size_t ldwork_cap = 0;
+    std::vector<char> ldwork_host;
     // bumped whenever a device buffer of the context is reallocated or a device
     // table (schedule, batch work tables) is re-uploaded: captured graphs check it
     uint64_t generation = 0;
@@ -217,6 +226,14 @@ hqa_status hqa_batch_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef*
                                const float* phi0, const float* p0, int M, float* phi_out,
                                float* p_out, float* phibar_out, cudaStream_t st);
 int hqa_sparse_pick_rb(const hqa_ctx* ctx, int32_t R, int prec);
+// batch_lowdeg.cu
+bool hqa_lowdeg_eligible(hqa_ctx* batch);
+size_t hqa_lowdeg_smem_bytes(const hqa_ctx* batch, int RB, int prec);
+int hqa_lowdeg_pick_rb(const hqa_ctx* batch, int32_t R, int prec);
+hqa_status hqa_lowdeg_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef* d_sched,
+                                int64_t S, int32_t W, int32_t R, uint64_t seed, int init,
+                                const float* phi0, const float* p0, int M, float* phi_out,
+                                float* p_out, float* phibar_out, cudaStream_t st);
 size_t hqa_sparse_smem_bytes(const hqa_ctx* ctx, int RB, int prec);
 hqa_status hqa_sparse_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const StepCoef* d_sched,
                                 int64_t S, int32_t W, int32_t R, uint64_t seed, int init,

@@ -4,8 +4,9 @@
 //
 // Candidates: the scalar sparse kernel at 1..32 replicas per block, the
 // vectorised sparse kernel at the blockings that fill a 16-byte vector, the
-// persistent batch kernel at 1..32 replicas per block (batch contexts), and
-// the dense tensor-core kernel (dense contexts in BF16 / BF16X2).  Each one
+// persistent batch kernels (list-streaming at 1..32 replicas per block, the
+// low-degree one at 1, 2, 4 where every member allows it), and the dense
+// tensor-core kernel (dense contexts in BF16 / BF16X2).  Each one
 // runs a short probe anneal (probe_steps leapfrog steps, dt = 1/probe_steps,
 // init PAPER) once untimed (plan build, caches) and then three times between
 // CUDA events on the caller's stream; the figure kept is the mean time per
@@ -31,6 +32,8 @@ std::vector<Cand> candidates(const hqa_ctx* ctx, int prec)
         return c;
     }
     for (int rb : rbs) c.push_back({HQA_KERNEL_SCALAR, rb});
+    if (ctx->is_batch && hqa_lowdeg_eligible(const_cast<hqa_ctx*>(ctx)) && prec != HQA_PREC_BF16X2)
+        for (int rb : {1, 2, 4}) c.push_back({HQA_KERNEL_LOWDEG, rb});
     if (!ctx->is_batch) {
         const int V = prec == HQA_PREC_BF16 ? 8 : 4;
         for (int rb : rbs)

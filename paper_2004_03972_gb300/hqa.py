@@ -24,7 +24,7 @@ STATUS_NAMES = {
 SCHED_PAPER, SCHED_LINEAR_GAMMA, SCHED_TABLE = 0, 1, 2
 INIT_PAPER, INIT_RANDOM_FLUX, INIT_GIVEN = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
-KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_DENSE = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_DENSE, KERNEL_LOWDEG = 0, 1, 2, 3, 4
 
 # every symbol include/hqa.h declares
 EXPORTS = (

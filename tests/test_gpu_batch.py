@@ -88,6 +88,64 @@ def test_batch_given_state_and_resume_bitwise(hqa):
         assert torch.equal(b[key], out[key]), key
 
 
+def test_lowdeg_kernel(hqa, orc):
+    """The low-degree batch kernel (lists, operand and state of a work item on chip):
+    the same bits at every replica blocking and as each member's own batch of one,
+    FP32 states within 1e-5 of the FP64 oracle (BF16 operand: 1e-2), and a run split
+    at step S1 equal to the whole run."""
+    insts = _members()
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, seed, dt = 6, 150, 21, 1 / 500
+    kw = dict(seed=seed, dt=dt, kernel=hqa.KERNEL_LOWDEG, outputs=("phi", "p", "phibar"))
+    runs = {rb: batch.run(S, R, replicas_per_block=rb, **kw) for rb in (1, 2, 4)}
+    bf = batch.run(S, R, replicas_per_block=2, precision=hqa.PREC_BF16, **kw)
+    batch.sync()
+    for rb in (2, 4):
+        for key in ("phi", "p", "phibar"):
+            assert torch.equal(runs[rb][key], runs[1][key]), (rb, key)
+    out = runs[2]
+    views = {key: batch.split(out[key], R) for key in ("phi", "p", "phibar")}
+    bviews = {key: batch.split(bf[key], R) for key in ("phi", "p")}
+    for k, c in enumerate(ctxs):
+        one = hqa.Context.batch([c])
+        alone = one.run(S, R, replicas_per_block=2, **dict(kw, seed=(seed + k * GOLD) & M64))
+        one.sync()
+        for key in views:
+            assert torch.equal(views[key][k], alone[key]), (k, key)
+        pr = orc.Problem.from_instance(insts[k])
+        for r in (0, R - 1):
+            ophi, op, _ = orc.md_run(pr, S, dt=dt, p0=orc.initial_momenta(member_seed(seed, k), r,
+                                                                          insts[k].N))
+            for tol, src in ((1e-5, views), (1e-2, bviews)):
+                g_phi = src["phi"][k][r].cpu().numpy().astype(np.float64)
+                g_p = src["p"][k][r].cpu().numpy().astype(np.float64)
+                assert np.max(np.abs(g_phi - ophi)) <= tol * np.max(np.abs(ophi)), (k, r, tol)
+                assert np.max(np.abs(g_p - op)) <= tol * max(1.0, np.max(np.abs(op))), (k, r, tol)
+    a = batch.run(40, R, replicas_per_block=2, **dict(kw, outputs=("phi", "p")))
+    b = batch.run(S - 40, R, replicas_per_block=2, init=hqa.INIT_GIVEN, phi0=a["phi"], p0=a["p"],
+                  start_step=40, **kw)
+    batch.sync()
+    for key in ("phi", "p", "phibar"):   # the window (100 steps) lies in the second call
+        assert torch.equal(b[key], out[key]), key
+
+
+def test_lowdeg_needs_low_degree(hqa):
+    ctxs = [hqa.Context.from_instance(instances.torus_pm1(6, 6, 1)),
+            hqa.Context.from_instance(instances.er_pm1(100, 0.1, 2))]   # degree ~10
+    batch = hqa.Context.batch(ctxs)
+    with pytest.raises(hqa.HQAError) as ei:
+        batch.run(20, 4, kernel=hqa.KERNEL_LOWDEG)
+    assert ei.value.status == 6
+    x = batch.run(20, 4, outputs=("phi",))                  # AUTO: the list-streaming kernel
+    y = batch.run(20, 4, outputs=("phi",), kernel=hqa.KERNEL_SCALAR)
+    batch.sync()
+    assert torch.equal(x["phi"], y["phi"])
+    single = hqa.Context.from_instance(instances.torus_pm1(6, 6, 1))
+    with pytest.raises(hqa.HQAError):
+        single.run(20, 4, kernel=hqa.KERNEL_LOWDEG)
+
+
 def test_batch_matches_oracle(hqa, orc):
     insts = _members()
     ctxs = [hqa.Context.from_instance(i) for i in insts]

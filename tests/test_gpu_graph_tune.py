@@ -154,10 +154,11 @@ def test_autotune_batch_and_errors(hqa):
     R = 32
     best, rows = b.autotune(R, probe_steps=16)
     ok = [r for r in rows if r[2] > 0]
-    assert ok and all(r[0] == hqa.KERNEL_SCALAR for r in rows)
-    assert best["replicas_per_block"] == min(ok, key=lambda r: r[2])[1]
+    assert ok and {r[0] for r in rows} == {hqa.KERNEL_SCALAR, hqa.KERNEL_LOWDEG}
+    fastest = min(ok, key=lambda r: r[2])
+    assert (best["kernel"], best["replicas_per_block"]) == (fastest[0], fastest[1])
     x = b.run(100, R, seed=2, outputs=("phi", "cut"))
-    y = b.run(100, R, seed=2, outputs=("phi", "cut"),
+    y = b.run(100, R, seed=2, outputs=("phi", "cut"), kernel=best["kernel"],
               replicas_per_block=best["replicas_per_block"])
     b.sync()
     assert torch.equal(x["phi"], y["phi"]) and torch.equal(x["cut"], y["cut"])
