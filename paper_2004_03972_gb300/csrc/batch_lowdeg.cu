@@ -10,8 +10,10 @@
 // flux operand ([N + 1][RB], FP32 or BF16), the FP32 flux master (BF16
 // operand only), the FP32 momentum and the window sums.  No global load is
 // left in the step loop, which the list-streaming kernel spends waiting on L2.
-// One thread per (spin, replica); the RB replicas of a spin sit in adjacent
-// lanes, so a spin's list is one broadcast shared load.
+// One thread per spin and pair of replicas (RB >= 2; one replica at RB = 1):
+// a spin's list is decoded once for both, each neighbour is one 8-byte (FP32)
+// or 4-byte (BF16) gather, and the state moves in pairs.  Every replica sees
+// the same floating-point operations at every blocking.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -117,19 +119,34 @@ __device__ __forceinline__ void st_op(uint32_t a, float v)
     }
 }
 
-// J_ij phi_j of one list entry u for replica r (u & 0x8000: J = -1)
-template <int RB, bool BF16>
-__device__ __forceinline__ float nb(uint32_t cur, uint32_t u, int r)
+// J_ij phi_j of one list entry u for replicas r0 .. r0 + PR - 1 (u & 0x8000:
+// J = -1), added into v[]
+template <int RB, int PR, bool BF16>
+__device__ __forceinline__ void nb(uint32_t cur, uint32_t u, int r0, float* v)
 {
     constexpr uint32_t ES = BF16 ? 2u : 4u;
-    const float v = ld_op<BF16>(cur + ((u & 0x7fffu) * RB + (uint32_t)r) * ES);
-    return (u & 0x8000u) ? -v : v;
+    const uint32_t a = cur + ((u & 0x7fffu) * RB + (uint32_t)r0) * ES;
+    const uint32_t sg = (u & 0x8000u) << 16;   // the FP32 sign bit
+    if constexpr (PR == 2 && !BF16) {
+        const uint2 x = lds64(a);
+        v[0] = __uint_as_float(x.x ^ sg);
+        v[1] = __uint_as_float(x.y ^ sg);
+    } else if constexpr (PR == 2) {
+        uint32_t x;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(x) : "r"(a));
+        v[0] = __uint_as_float((x << 16) ^ sg);
+        v[1] = __uint_as_float((x & 0xffff0000u) ^ sg);
+    } else {
+        v[0] = __uint_as_float(__float_as_uint(ld_op<BF16>(a)) ^ sg);
+    }
 }
 
 template <int RB, bool BF16>
 __global__ void __launch_bounds__(kLdThreads, 1) k_batch_lowdeg(const LdArgs a)
 {
     constexpr uint32_t ES = BF16 ? 2u : 4u;
+    constexpr int PR = RB >= 2 ? 2 : 1;   // replicas per thread
+    constexpr int TR = RB / PR;           // threads per spin
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
@@ -192,24 +209,59 @@ __global__ void __launch_bounds__(kLdThreads, 1) k_batch_lowdeg(const LdArgs a)
             const uint32_t cur = s0 + (uint32_t)(j & 1) * buf;
             const uint32_t nxt = s0 + (uint32_t)((j & 1) ^ 1) * buf;
             const bool in_win = j >= win0;
-            for (int idx = t; idx < NRB; idx += kLdThreads) {
-                const int row = idx / RB, r = idx % RB;
+            for (int idx = t; idx < N * TR; idx += kLdThreads) {
+                const int row = idx / TR, r0 = (idx % TR) * PR;
                 const uint2 l = lds64(sl + (uint32_t)row * 8u);
-                float L = (nb<RB, BF16>(cur, l.x & 0xffffu, r) + nb<RB, BF16>(cur, l.x >> 16, r)) +
-                          (nb<RB, BF16>(cur, l.y & 0xffffu, r) + nb<RB, BF16>(cur, l.y >> 16, r));
-                const uint32_t e = (uint32_t)idx;
-                const float phi = BF16 ? lds32(master + e * 4u) : lds32(cur + e * 4u);
-                if (m.h) L += 2.f * lds32(sh + (uint32_t)row * 4u) * fabsf(phi);
-                const float phi2 = phi * phi;
-                float pw = phi;
-                for (int q = 0; q < mhalf; ++q) pw *= phi2;
-                float p = lds32(sp + e * 4u);
-                p = p - fmaf(cf.x, pw, cf.y * L);
-                const float phin = fmaf(cf.z, p, phi);
-                sts32(sp + e * 4u, p);
-                if constexpr (BF16) sts32(master + e * 4u, phin);
-                st_op<BF16>(nxt + e * ES, phin);
-                if (in_win) sts32(sw + e * 4u, lds32(sw + e * 4u) + phin);
+                float v0[PR], v1[PR], v2[PR], v3[PR];
+                nb<RB, PR, BF16>(cur, l.x & 0xffffu, r0, v0);
+                nb<RB, PR, BF16>(cur, l.x >> 16, r0, v1);
+                nb<RB, PR, BF16>(cur, l.y & 0xffffu, r0, v2);
+                nb<RB, PR, BF16>(cur, l.y >> 16, r0, v3);
+                const uint32_t e = (uint32_t)(row * RB + r0);
+                float phi[PR], p[PR], phin[PR];
+                if constexpr (PR == 2) {
+                    const uint2 f = lds64((BF16 ? master : cur) + e * 4u);
+                    const uint2 q = lds64(sp + e * 4u);
+                    phi[0] = __uint_as_float(f.x);
+                    phi[1] = __uint_as_float(f.y);
+                    p[0] = __uint_as_float(q.x);
+                    p[1] = __uint_as_float(q.y);
+                } else {
+                    phi[0] = lds32((BF16 ? master : cur) + e * 4u);
+                    p[0] = lds32(sp + e * 4u);
+                }
+                const float hr = m.h ? 2.f * lds32(sh + (uint32_t)row * 4u) : 0.f;
+#pragma unroll
+                for (int k = 0; k < PR; ++k) {
+                    float L = (v0[k] + v1[k]) + (v2[k] + v3[k]);
+                    if (m.h) L += hr * fabsf(phi[k]);
+                    const float phi2 = phi[k] * phi[k];
+                    float pw = phi[k];
+                    for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                    p[k] = p[k] - fmaf(cf.x, pw, cf.y * L);
+                    phin[k] = fmaf(cf.z, p[k], phi[k]);
+                }
+                if constexpr (PR == 2) {
+                    sts64(sp + e * 4u, make_uint2(__float_as_uint(p[0]), __float_as_uint(p[1])));
+                    const uint2 fn = make_uint2(__float_as_uint(phin[0]), __float_as_uint(phin[1]));
+                    if constexpr (BF16) {
+                        sts64(master + e * 4u, fn);
+                        st_op<BF16>(nxt + e * ES, phin[0]);
+                        st_op<BF16>(nxt + (e + 1u) * ES, phin[1]);
+                    } else {
+                        sts64(nxt + e * 4u, fn);
+                    }
+                    if (in_win) {
+                        const uint2 w = lds64(sw + e * 4u);
+                        sts64(sw + e * 4u, make_uint2(__float_as_uint(__uint_as_float(w.x) + phin[0]),
+                                                      __float_as_uint(__uint_as_float(w.y) + phin[1])));
+                    }
+                } else {
+                    sts32(sp + e * 4u, p[0]);
+                    if constexpr (BF16) sts32(master + e * 4u, phin[0]);
+                    st_op<BF16>(nxt + e * ES, phin[0]);
+                    if (in_win) sts32(sw + e * 4u, lds32(sw + e * 4u) + phin[0]);
+                }
             }
             __syncthreads();
         }
