@@ -178,7 +178,9 @@ hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const 
  * uneven size, e.g. the paper's ensembles of random instances).  The members
  * are not copied: they must outlive the batch and not be destroyed first.
  * hqa_run on a batch runs `replicas` replicas of every member in one
- * persistent launch (work items = member x replica block, longest first).
+ * persistent launch (work items = member x replica block, longest first):
+ * HQA_KERNEL_LOWDEG when every member has at most 4 couplings per spin,
+ * else the list-streaming kernel (HQA_KERNEL_SCALAR).
  * Batch array layout: member k's [R][N_k] block starts at R * (N_0 + ... +
  * N_{k-1}); per-replica results (energy, cut, tally) are [count][R].  Member
  * k draws its momenta from the stream seed + (k + 1) * 0x632BE59BD9B4E019
@@ -429,8 +431,9 @@ hqa_status hqa_hmd(hqa_ctx* ctx, const hqa_schedule* sched, double tau, int32_t 
 /* Autotuner: times each launch shape hqa_run can use for `replicas`
  * replicas at opts->precision (NULL = defaults) -- the scalar sparse kernel
  * at 1, 2, 4, ..., 32 replicas per block, the vectorised one at the
- * blockings that fill a 16-byte vector, the persistent batch kernel at
- * 1..32 (batch contexts), the dense tensor-core kernel (dense BF16/BF16X2)
+ * blockings that fill a 16-byte vector, the persistent batch kernels
+ * (batch contexts: list-streaming at 1..32, HQA_KERNEL_LOWDEG at 1, 2, 4
+ * when every member allows it), the dense tensor-core kernel (dense BF16/BF16X2)
  * -- on a probe anneal of probe_steps steps (1..100000; dt = 1/probe_steps,
  * init PAPER), one untimed run then three between CUDA events on `stream`.
  * The fastest is written to *best (the other fields from opts) and kept in
