@@ -141,6 +141,39 @@ __device__ __forceinline__ void nb(uint32_t cur, uint32_t u, int r0, float* v)
     }
 }
 
+// Packed FP32 pairs (Blackwell's f32x2 arithmetic: each half rounds like the
+// scalar instruction, so a pair gets the bits of two scalar evaluations).
+__device__ __forceinline__ uint64_t pk(float x, float y)
+{
+    return (uint64_t)__float_as_uint(x) | ((uint64_t)__float_as_uint(y) << 32);
+}
+__device__ __forceinline__ float lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 template <int RB, bool BF16>
 __global__ void __launch_bounds__(kLdThreads, 1) k_batch_lowdeg(const LdArgs a)
 {
@@ -231,15 +264,32 @@ __global__ void __launch_bounds__(kLdThreads, 1) k_batch_lowdeg(const LdArgs a)
                     p[0] = lds32(sp + e * 4u);
                 }
                 const float hr = m.h ? 2.f * lds32(sh + (uint32_t)row * 4u) : 0.f;
-#pragma unroll
-                for (int k = 0; k < PR; ++k) {
-                    float L = (v0[k] + v1[k]) + (v2[k] + v3[k]);
-                    if (m.h) L += hr * fabsf(phi[k]);
-                    const float phi2 = phi[k] * phi[k];
-                    float pw = phi[k];
-                    for (int q = 0; q < mhalf; ++q) pw *= phi2;
-                    p[k] = p[k] - fmaf(cf.x, pw, cf.y * L);
-                    phin[k] = fmaf(cf.z, p[k], phi[k]);
+                // the same operations, in pairs or alone:
+                //   L = (v0 + v1) + (v2 + v3) [+ 2h|phi| by fma]; pw = phi^(M-1)
+                //   p -= fma(kA, pw, kB L); phi' = fma(dA, p, phi)
+                if constexpr (PR == 2) {
+                    const uint64_t f = pk(phi[0], phi[1]);
+                    uint64_t L = add2(add2(pk(v0[0], v0[1]), pk(v1[0], v1[1])),
+                                      add2(pk(v2[0], v2[1]), pk(v3[0], v3[1])));
+                    if (m.h) L = fma2(pk(hr, hr), pk(fabsf(phi[0]), fabsf(phi[1])), L);
+                    const uint64_t f2 = mul2(f, f);
+                    uint64_t pw = f;
+                    for (int q = 0; q < mhalf; ++q) pw = mul2(pw, f2);
+                    const uint64_t pp = sub2(pk(p[0], p[1]),
+                                             fma2(pk(cf.x, cf.x), pw, mul2(pk(cf.y, cf.y), L)));
+                    const uint64_t fn = fma2(pk(cf.z, cf.z), pp, f);
+                    p[0] = lo(pp);
+                    p[1] = hi(pp);
+                    phin[0] = lo(fn);
+                    phin[1] = hi(fn);
+                } else {
+                    float L = (v0[0] + v1[0]) + (v2[0] + v3[0]);
+                    if (m.h) L = fmaf(hr, fabsf(phi[0]), L);
+                    const float phi2 = __fmul_rn(phi[0], phi[0]);
+                    float pw = phi[0];
+                    for (int q = 0; q < mhalf; ++q) pw = __fmul_rn(pw, phi2);
+                    p[0] = __fsub_rn(p[0], fmaf(cf.x, pw, __fmul_rn(cf.y, L)));
+                    phin[0] = fmaf(cf.z, p[0], phi[0]);
                 }
                 if constexpr (PR == 2) {
                     sts64(sp + e * 4u, make_uint2(__float_as_uint(p[0]), __float_as_uint(p[1])));
@@ -253,8 +303,8 @@ __global__ void __launch_bounds__(kLdThreads, 1) k_batch_lowdeg(const LdArgs a)
                     }
                     if (in_win) {
                         const uint2 w = lds64(sw + e * 4u);
-                        sts64(sw + e * 4u, make_uint2(__float_as_uint(__uint_as_float(w.x) + phin[0]),
-                                                      __float_as_uint(__uint_as_float(w.y) + phin[1])));
+                        const uint64_t ws = add2((uint64_t)w.x | ((uint64_t)w.y << 32), pk(phin[0], phin[1]));
+                        sts64(sw + e * 4u, make_uint2((uint32_t)ws, (uint32_t)(ws >> 32)));
                     }
                 } else {
                     sts32(sp + e * 4u, p[0]);
