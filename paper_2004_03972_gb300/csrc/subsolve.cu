@@ -421,6 +421,9 @@ __global__ void __launch_bounds__(kEnumThreads) k_sub_enum16_min(const SubPrep* 
 }
 
 // Phase 2: the threads that reached the replica minimum find its smallest x.
+// A warp walks each of its candidates' ranges together: lane l takes the
+// sub-range whose next five bits equal l, so a candidate costs 1/32 of its
+// phase-1 walk; the smallest x attaining the minimum wins by atomicMin.
 __global__ void __launch_bounds__(kEnumThreads) k_sub_enum16_arg(const SubPrep* __restrict__ prep,
                                                                  int LBreq, const int16_t* tmin,
                                                                  const int* emin,
@@ -436,14 +439,27 @@ __global__ void __launch_bounds__(kEnumThreads) k_sub_enum16_arg(const SubPrep* 
     const int LB = LBreq < n ? LBreq : n;
     const int HB = n - LB;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u;
     const int target = emin[r];
-    if (LB < 3 || tid >= (1u << HB)) return;
-    if ((int)tmin[(size_t)r * gridDim.x * blockDim.x + tid] != target) return;
-    const uint32_t bx =
-        packed_walk<2>(s_nz, s_ng, s_pc, s_he, s_cA, s_cB, s_nA, s_nB, n, LB, tid << LB, target,
-                       nullptr);
-    if (bx != 0xffffffffu)
-        atomicMin(keys + r, ((unsigned long long)((uint32_t)target ^ 0x80000000u) << 32) | bx);
+    if (LB < 3) return;
+    const bool cand = tid < (1u << HB) &&
+                      (int)tmin[(size_t)r * gridDim.x * blockDim.x + tid] == target;
+    const unsigned long long hi = (unsigned long long)((uint32_t)target ^ 0x80000000u) << 32;
+    if (LB < 8) {   // too few bits to share: each candidate walks its own range
+        if (!cand) return;
+        const uint32_t bx = packed_walk<2>(s_nz, s_ng, s_pc, s_he, s_cA, s_cB, s_nA, s_nB, n, LB,
+                                           tid << LB, target, nullptr);
+        if (bx != 0xffffffffu) atomicMin(keys + r, hi | bx);
+        return;
+    }
+    const int SB = LB - 5;
+    for (unsigned bal = __ballot_sync(0xffffffffu, cand); bal; bal &= bal - 1) {
+        const uint32_t ct = (tid & ~31u) | (uint32_t)(__ffs(bal) - 1);   // the candidate
+        const uint32_t bx = packed_walk<2>(s_nz, s_ng, s_pc, s_he, s_cA, s_cB, s_nA, s_nB, n, SB,
+                                           (ct << LB) | (lane << SB), target, nullptr);
+        const uint32_t m = __reduce_min_sync(0xffffffffu, bx);
+        if (lane == 0 && m != 0xffffffffu) atomicMin(keys + r, hi | m);
+    }
 }
 
 // Writes the assembled configuration.
