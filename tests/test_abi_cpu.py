@@ -77,6 +77,32 @@ def test_struct_layout_matches_header(tmp_path):
             assert getattr(table[t], f).offset == int(v), (t, f)
 
 
+def test_enum_constants_match_header(tmp_path):
+    """The binding's constants equal the header's enumerators (a host program
+    compiled from include/hqa.h prints them)."""
+    from paper_2004_03972_gb300 import hqa
+    pairs = {f"HQA_{k}": v for k, v in (
+        ("SCHED_PAPER", hqa.SCHED_PAPER), ("SCHED_LINEAR_GAMMA", hqa.SCHED_LINEAR_GAMMA),
+        ("SCHED_TABLE", hqa.SCHED_TABLE), ("INIT_PAPER", hqa.INIT_PAPER),
+        ("INIT_RANDOM_FLUX", hqa.INIT_RANDOM_FLUX), ("INIT_GIVEN", hqa.INIT_GIVEN),
+        ("PREC_FP32", hqa.PREC_FP32), ("PREC_BF16", hqa.PREC_BF16),
+        ("PREC_BF16X2", hqa.PREC_BF16X2), ("KERNEL_AUTO", hqa.KERNEL_AUTO),
+        ("KERNEL_SCALAR", hqa.KERNEL_SCALAR), ("KERNEL_VECTOR", hqa.KERNEL_VECTOR),
+        ("KERNEL_DENSE", hqa.KERNEL_DENSE), ("KERNEL_LOWDEG", hqa.KERNEL_LOWDEG),
+        ("MLP_IN", hqa.MLP_IN), ("MLP_HIDDEN", hqa.MLP_HIDDEN), ("MLP_OUT", hqa.MLP_OUT),
+        ("MLP_PARAMS", hqa.MLP_PARAMS))}
+    pairs.update({name: code for code, name in hqa.STATUS_NAMES.items()})
+    src = tmp_path / "enums.c"
+    src.write_text('#include <stdio.h>\n#include "hqa.h"\nint main(void) {\n'
+                   + "".join(f' printf("{n} %d\\n", (int)({n}));\n' for n in pairs)
+                   + " return 0; }\n")
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    values = dict(zip(got[0::2], map(int, got[1::2])))
+    assert values == pairs
+
+
 def test_library_has_no_cuda_runtime_dependency(lib):
     from paper_2004_03972_gb300 import hqa
     out = subprocess.run(["ldd", hqa.LIB_PATH], capture_output=True, text=True).stdout
