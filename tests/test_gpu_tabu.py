@@ -70,6 +70,25 @@ def test_tabu_bit_exact_given_configurations(hqa, orc, hmax):
         assert int(te[r]) == we
 
 
+def test_tabu_hand_traced_triangle(hqa):
+    """The hand-traced trajectory of tests/golden/tabu_triangle.txt, on the GPU."""
+    import os
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                          "tabu_triangle.txt")
+    J = -np.ones((3, 3)) + np.eye(3)
+    ctx = hqa.Context.from_instance(instances.Instance("triangle", 3, dense=J, h=np.ones(3)))
+    s = torch.ones((1, 3), dtype=torch.int8, device="cuda")
+    f = torch.zeros((1, 3), dtype=torch.uint8, device="cuda")
+    for line in open(golden):
+        if not line.strip() or line.startswith("#"):
+            continue
+        tenure, iters, e_best, spins = line.split()
+        out, e = ctx.solve_sub_tabu(s, f, 3, int(iters), int(tenure))
+        ctx.sync()
+        assert int(e[0]) == int(e_best), (tenure, iters)
+        assert out[0].cpu().tolist() == [int(v) for v in spins.split(",")], (tenure, iters)
+
+
 def test_tabu_against_exact_on_small_sets(hqa, orc):
     inst = instances.er_pm1(800, 0.06, 1200)
     ctx = hqa.Context.from_instance(inst)

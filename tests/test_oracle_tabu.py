@@ -6,11 +6,32 @@ exact enumeration is out of reach):
     above the input's, never touches a frozen spin, and reports the energy of what
     it returns
   * with enough iterations on small sets it reaches the exact optimum
+  * a hand-traced trajectory (tests/golden/tabu_triangle.txt): the uphill escape
+    from a local minimum, the smallest-index tie-break, the tabu expiry
+    until < it, the strict aspiration, and the cycling of tenure 0
 """
+import os
+
 import numpy as np
 import pytest
 
 from paper_2004_03972_gb300 import instances
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tabu_triangle.txt")
+
+
+def test_hand_traced_triangle(orc):
+    J = -np.ones((3, 3)) + np.eye(3)
+    inst = instances.Instance("triangle", 3, dense=J, h=np.ones(3))
+    pr = orc.Problem.from_instance(inst)
+    s = np.ones(3, np.int8)
+    f = np.zeros(3, np.uint8)
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 6
+    for tenure, iters, e_best, spins in rows:
+        out, e = orc.subsolve_tabu(pr, s, f, int(iters), int(tenure))
+        assert e == int(e_best), (tenure, iters)
+        assert out.tolist() == [int(v) for v in spins.split(",")], (tenure, iters)
 
 
 def _case(orc, seed, N=120, n=8):
