@@ -350,7 +350,7 @@ cudaError_t launch_ld(const LdArgs& a, int grid, size_t smem, cudaStream_t st)
 
 // Every member has at most four couplings per spin, each -1 or +1, and fewer
 // than 2^15 spins (host-only check, cached).
-bool hqa_lowdeg_eligible(hqa_ctx* b)
+bool hqa_lowdeg_eligible(const hqa_ctx* b)
 {
     if (!b->is_batch) return false;
     if (b->ld_state == 0) {

@@ -158,7 +158,7 @@ struct hqa_ctx {
     std::vector<char> bwork_host;   // what d_bwork holds (tables are uploaded only on change)
     // low-degree batch kernel: eligibility (0 unknown, 1 yes, -1 no), the members'
     // compact lists (built once) and per-run tables
-    int ld_state = 0;
+    mutable int ld_state = 0;
     void* d_ld = nullptr;
     size_t ld_cap = 0;
     std::vector<int64_t> ld_off;
@@ -227,7 +227,7 @@ hqa_status hqa_batch_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef*
                                float* p_out, float* phibar_out, cudaStream_t st);
 int hqa_sparse_pick_rb(const hqa_ctx* ctx, int32_t R, int prec);
 // batch_lowdeg.cu
-bool hqa_lowdeg_eligible(hqa_ctx* batch);
+bool hqa_lowdeg_eligible(const hqa_ctx* batch);
 size_t hqa_lowdeg_smem_bytes(const hqa_ctx* batch, int RB, int prec);
 int hqa_lowdeg_pick_rb(const hqa_ctx* batch, int32_t R, int prec);
 hqa_status hqa_lowdeg_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef* d_sched,

@@ -32,7 +32,7 @@ std::vector<Cand> candidates(const hqa_ctx* ctx, int prec)
         return c;
     }
     for (int rb : rbs) c.push_back({HQA_KERNEL_SCALAR, rb});
-    if (ctx->is_batch && hqa_lowdeg_eligible(const_cast<hqa_ctx*>(ctx)) && prec != HQA_PREC_BF16X2)
+    if (ctx->is_batch && hqa_lowdeg_eligible(ctx) && prec != HQA_PREC_BF16X2)
         for (int rb : {1, 2, 4}) c.push_back({HQA_KERNEL_LOWDEG, rb});
     if (!ctx->is_batch) {
         const int V = prec == HQA_PREC_BF16 ? 8 : 4;
