@@ -205,3 +205,21 @@ def test_first_half_kick_with_zero_flux_keeps_momenta(orc):
     alpha_half, _ = orc.schedule(0.5)
     assert np.array_equal(p, p0)
     assert np.allclose(phi, alpha_half * p0, rtol=1e-15)
+
+
+def test_replica_driver_equals_single_runs(orc):
+    """The OpenMP replica driver (the CPU baseline and reference arm) runs each
+    replica's trajectory on its own: the same bits as md_run per replica, at one
+    thread and at several, from paper and from random initial fluxes."""
+    inst = instances.with_integer_field(instances.er_pm1(90, 0.1, 7), 2, 8)
+    pr = orc.Problem.from_instance(inst)
+    R, S = 5, 60
+    p0 = np.stack([orc.initial_momenta(11, r, inst.N) for r in range(R)])
+    phi0 = np.stack([orc.initial_flux_random(11, r, inst.N) for r in range(R)])
+    for start in (np.zeros_like(p0), phi0):
+        runs = [orc.md_run_replicas(pr, S, start, p0, threads=t) for t in (1, 4)]
+        for r in range(R):
+            one = orc.md_run(pr, S, phi0=start[r], p0=p0[r])
+            for t in range(2):
+                for k in range(3):
+                    assert np.array_equal(runs[t][k][r], one[k]), (r, t, k)
