@@ -484,10 +484,11 @@ def run_ours(args):
                 "bound": "issue: two block-wide argmins and 2 barriers per flip, row loads from L2"}
     cpu = cpu_baseline(args, inst, cfg) if (rank == 0 and not args.skip_cpu) else None
     # launches per pipeline step: MD (+ init and output copy per chunk on the dense
-    # path), readout, energy; the exact sub-solve adds prep, packed minimum, packed
-    # argmin, scalar walk (returns at once for packed replicas), assemble and energy
-    launches = (3 * plan.get("chunks", 1) if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + 1 + \
-        (0 if batch or real else 6)
+    # path), readout, energy (real couplings: spin masks, fixed-point sums, rounding);
+    # the exact sub-solve adds prep, packed minimum, packed argmin, scalar walk
+    # (returns at once for packed replicas), assemble and energy
+    launches = (3 * plan.get("chunks", 1) if plan["kernel"] == hqa.KERNEL_DENSE else 1) + 1 + \
+        (3 if real else 1) + (0 if batch or real else 6)
     line = {
         "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_pipe / args.steps,
