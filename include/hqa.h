@@ -163,7 +163,9 @@ void hqa_run_opts_default(hqa_run_opts* o);
 hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t flags,
                             hqa_ctx** out);
 
-/* Creates a context from CSR couplings (host arrays).
+/* Creates a context from CSR couplings (host arrays): the Ising problem of
+ * Results Eq. (1) with sparse symmetric J, e.g. the weighted graphs of the
+ * MAX-CUT mapping (Methods, "MAX-CUT and Ising spin-glass": J_ij = w_ij, h = 0).
  *   row_ptr  N+1 int64, row_ptr[0] = 0, non-decreasing, row_ptr[N] = nnz
  *   col      nnz int32 in [0, N); duplicates within a row are rejected
  *   val      nnz float
@@ -175,7 +177,10 @@ hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const 
                           const float* val, const float* h, uint32_t flags, hqa_ctx** out);
 
 /* Creates a batch context over `count` existing contexts (instances of
- * uneven size, e.g. the paper's ensembles of random instances).  The members
+ * uneven size).  The paper runs ensembles of random instances, each its own
+ * problem of Results Eq. (1) (Results, "HQA for MAX-CUT": 100 random K2000
+ * instances; "HQA for Ising spin-glass"); a batch runs many such instances
+ * in one launch, which the paper does not do.  The members
  * are not copied: they must outlive the batch and not be destroyed first.
  * hqa_run on a batch runs `replicas` replicas of every member in one
  * persistent launch (work items = member x replica block, longest first):
@@ -302,12 +307,17 @@ hqa_status hqa_solve_sub_tabu(hqa_ctx* ctx, int32_t replicas, const int8_t* spin
  * counterpart: this exists for callers that cannot let the library call
  * cudaMalloc -- a process whose device memory is already reserved by
  * another allocator or arena, or a latency-sensitive caller that cannot
- * accept cudaMalloc's implicit device-wide synchronisation.  Same arguments,
- * results and errors as hqa_solve_sub; the caller still provides every
- * input and output buffer.
+ * accept cudaMalloc's implicit device-wide synchronisation.  Same arguments
+ * and results as hqa_solve_sub, and its errors checked in the same order;
+ * after them come the two of this variant: replicas > 2048 returns
+ * HQA_ERR_TOO_LARGE and a current device other than the context's returns
+ * HQA_ERR_INVALID_ARG.  The caller still provides every input and output
+ * buffer.  Every replica takes the scalar Gray-code walk: hqa_solve_sub's
+ * faster packed 16-bit walk keeps per-thread minima whose size grows with the
+ * enumeration and does not fit the fixed scratch.  The results are the same.
  * Scratch: a fixed array compiled into the library (about 1.1 MB, enough for
  * 2048 replicas), present on every GPU that loads the library until the
- * process exits.  replicas > 2048 returns HQA_ERR_TOO_LARGE.
+ * process exits.
  * The first call on a device looks up that array's device address (once per
  * device, with the context's device current); make that first call before
  * any stream capture.  The current device must be the context's device

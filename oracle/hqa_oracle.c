@@ -556,6 +556,23 @@ double or_mlp_loss_grad(int64_t n, const double* x, const double* y, const doubl
     return loss / (double)n;
 }
 
+/* AdamW (Loshchilov and Hutter, "Decoupled weight decay regularization",
+ * ICLR 2019), step t >= 1 on P parameters, in place, FP64:
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   mhat = m / (1 - b1^t),   vhat = v / (1 - b2^t),
+ *   w <- w - lr (mhat / (sqrt(vhat) + eps) + wd w). */
+void or_adamw(int64_t P, double* w, const double* g, double* m, double* v, int64_t t, double lr,
+              double b1, double b2, double eps, double wd)
+{
+    const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (int64_t k = 0; k < P; ++k) {
+        m[k] = b1 * m[k] + (1.0 - b1) * g[k];
+        v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+        const double mh = m[k] / c1, vh = v[k] / c2;
+        w[k] = w[k] - lr * (mh / (sqrt(vh) + eps) + wd * w[k]);
+    }
+}
+
 
 /* ------------------------------------------------------------------ */
 /* Tabu search on the reduced problem, for ambivalent sets too large to   */

@@ -82,6 +82,8 @@ def _load():
             lib.or_subsolve_tabu.restype = i64
             lib.or_mlp_loss_grad.argtypes = [i64, vp, vp, vp, vp, vp]
             lib.or_mlp_loss_grad.restype = d
+            lib.or_adamw.argtypes = [i64, vp, vp, vp, vp, i64, d, d, d, d, d]
+            lib.or_adamw.restype = None
             _lib = lib
     return _lib
 
@@ -273,6 +275,20 @@ def mlp_loss_grad(x, y, params, want_grad=True):
     z = np.empty((n, MLP_OUT))
     loss = _load().or_mlp_loss_grad(n, _ptr(x), _ptr(y), _ptr(params), _ptr(g), _ptr(z))
     return float(loss), g, z
+
+
+def adamw(params, grads, lr, beta1, beta2, eps, weight_decay):
+    """AdamW from zero moments: applies the gradients ``grads`` (a sequence of [P]
+    arrays) as steps t = 1, 2, ... and returns the parameters after each step."""
+    w = np.array(params, dtype=np.float64)
+    m, v = np.zeros_like(w), np.zeros_like(w)
+    out = []
+    for t, g in enumerate(grads, 1):
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        _load().or_adamw(w.size, _ptr(w), _ptr(g), _ptr(m), _ptr(v), t, float(lr), float(beta1),
+                         float(beta2), float(eps), float(weight_decay))
+        out.append(w.copy())
+    return out
 
 
 # ---------------------------------------------------------------------------

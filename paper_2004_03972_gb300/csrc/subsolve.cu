@@ -534,10 +534,13 @@ hqa_status hqa_launch_subsolve(hqa_ctx* ctx, int32_t R, const int8_t* spins,
 // memory is reserved up front by another allocator or arena (nothing is left
 // to hand out), and latency-sensitive callers for whom cudaMalloc's implicit
 // device-wide synchronisation is not acceptable.  This entry point runs the
-// same three kernels as hqa_solve_sub, but its scratch (the per-replica
-// reduced-problem records and the 64-bit argmin keys) lives in the
-// file-scope array below, which every GPU that loads the library holds until
-// the process exits.  The records and keys of each replica are rewritten by
+// preparation, the scalar Gray-code walk and the assembly of hqa_solve_sub
+// (plus the energy kernel when asked), but not its packed 16-bit walk: that
+// walk's per-thread minima grow with the enumeration and do not fit a fixed
+// array, so every replica takes the scalar walk, which is slower but reaches
+// the same (H', x) minimum.  Its scratch (the per-replica reduced-problem
+// records and the 64-bit argmin keys) lives in the file-scope array below,
+// which every GPU that loads the library holds until the process exits.  The records and keys of each replica are rewritten by
 // k_sub_prep before they are read, so stale contents from the previous call
 // are never used.  All calls share the one array: calls whose kernels
 // overlap on the GPU (e.g. on two streams) race and must be serialised by
@@ -581,23 +584,23 @@ static hqa_status sub_scratch_address(int dev, unsigned char** out)
     return HQA_OK;
 }
 
-extern "C" hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
-                                            const uint8_t* frozen, int32_t n, int8_t* out_spins,
-                                            int64_t* out_energy, void* stream)
+static hqa_status solve_sub_noalloc_impl(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                                         const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                                         int64_t* out_energy, void* stream)
 {
-    if (!ctx || replicas < 1 || !spins || !frozen || !out_spins || n < 0) return HQA_ERR_INVALID_ARG;
-    if (ctx->is_batch) return HQA_ERR_UNSUPPORTED;  // a batch has no coupling arrays of its own
-    if (out_energy && ((uintptr_t)out_energy % 8) != 0) return HQA_ERR_INVALID_ARG;
-    if (replicas > kNoAllocMaxReplicas) return HQA_ERR_TOO_LARGE;  // scratch holds 2048 replicas
+    // the checks of hqa_solve_sub, in its order, then the two of this variant
+    if (ctx && ctx->is_batch) return HQA_ERR_UNSUPPORTED;  // a batch has no coupling arrays of its own
+    if (!ctx || replicas < 1 || !spins || !frozen || !out_spins) return HQA_ERR_INVALID_ARG;
+    if (n < 0 || (out_energy && ((uintptr_t)out_energy % 8) != 0)) return HQA_ERR_INVALID_ARG;
     if (!ctx->integer || !ctx->unit) return HQA_ERR_UNSUPPORTED;
     if (n > kMaxN) return HQA_ERR_TOO_LARGE;
+    if (replicas > kNoAllocMaxReplicas) return HQA_ERR_TOO_LARGE;  // scratch holds 2048 replicas
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return HQA_ERR_CUDA;
     }
     if (dev != ctx->device) return HQA_ERR_INVALID_ARG;  // the scratch address is per device
-    hqa_capture_touch(ctx);
     unsigned char* base = nullptr;
     hqa_status s = sub_scratch_address(dev, &base);
     if (s != HQA_OK) return s;
@@ -616,4 +619,13 @@ extern "C" hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, cons
     if (cudaGetLastError() != cudaSuccess) return HQA_ERR_CUDA;
     if (out_energy) return hqa_launch_energy(ctx, R, out_spins, out_energy, nullptr, st);
     return HQA_OK;
+}
+
+extern "C" hqa_status hqa_solve_sub_noalloc(hqa_ctx* ctx, int32_t replicas, const int8_t* spins,
+                                            const uint8_t* frozen, int32_t n, int8_t* out_spins,
+                                            int64_t* out_energy, void* stream)
+{
+    hqa_capture_touch(ctx);
+    return hqa_capture_note(
+        solve_sub_noalloc_impl(ctx, replicas, spins, frozen, n, out_spins, out_energy, stream));
 }

@@ -394,7 +394,30 @@ class Context:
     def solve_sub_noalloc(self, spins, frozen, n, out_spins, out_energy=None, stream=None):
         """hqa_solve_sub_noalloc: the sub-solve with the library's fixed scratch array,
         for callers that cannot let the library allocate device memory.  The caller
-        passes the output buffers; nothing is allocated here or in the library."""
+        passes the output buffers; nothing is allocated here or in the library.
+        The library writes R*N int8 spins and R int64 energies through the raw
+        pointers, so every buffer is checked first: spins and out_spins int8 (R, N),
+        frozen uint8 (R, N), out_energy None or int64 (R,), all contiguous and on one
+        CUDA device (ValueError otherwise)."""
+        import torch
+        if spins.dim() != 2 or spins.shape[1] != self.N:
+            raise ValueError(f"spins must have shape (R, {self.N})")
+        R = spins.shape[0]
+        want = [("spins", spins, torch.int8, (R, self.N)),
+                ("frozen", frozen, torch.uint8, (R, self.N)),
+                ("out_spins", out_spins, torch.int8, (R, self.N))]
+        if out_energy is not None:
+            want.append(("out_energy", out_energy, torch.int64, (R,)))
+        for name, t, dtype, shape in want:
+            if not isinstance(t, torch.Tensor):
+                raise ValueError(f"{name} must be a torch tensor")
+            if t.dtype != dtype or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be {dtype} of shape {shape}, got {t.dtype} "
+                                 f"{tuple(t.shape)}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+            if t.device.type != "cuda" or t.device != spins.device:
+                raise ValueError(f"{name} must be on {spins.device} (a CUDA device)")
         _check(lib().hqa_solve_sub_noalloc(self._h, spins.shape[0], _ptr(spins), _ptr(frozen),
                                            int(n), _ptr(out_spins), _ptr(out_energy),
                                            _stream_ptr(stream)), "hqa_solve_sub_noalloc")

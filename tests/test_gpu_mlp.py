@@ -59,23 +59,18 @@ def test_forward_and_gradient_bf16(hqa, orc):
     assert np.max(np.abs(gg - g_ref)) <= 5e-2 * np.max(np.abs(g_ref))
 
 
-def test_adamw_step_formula(hqa):
+def test_adamw_step_matches_oracle(hqa, orc):
     w = hqa.MLP.init_params(5)
     mlp = hqa.MLP(w)
     rng = np.random.default_rng(2)
     gs = [rng.normal(size=hqa.MLP_PARAMS).astype(np.float32) for _ in range(3)]
     lr, b1, b2, eps, wd = 1e-2, 0.9, 0.99, 1e-6, 1e-3
-    m = np.zeros_like(w, dtype=np.float64)
-    v = np.zeros_like(m)
-    ref = w.astype(np.float64)
-    for t, g in enumerate(gs, 1):
+    refs = orc.adamw(w.astype(np.float64), gs, lr, b1, b2, eps, wd)
+    for g, ref in zip(gs, refs):
         mlp.adamw(torch.from_numpy(g).cuda(), lr, b1, b2, eps, wd)
-        m = b1 * m + (1 - b1) * g
-        v = b2 * v + (1 - b2) * g.astype(np.float64) ** 2
-        mh, vh = m / (1 - b1 ** t), v / (1 - b2 ** t)
-        ref = ref - lr * (mh / (np.sqrt(vh) + eps) + wd * ref)
-    torch.cuda.synchronize()
-    assert np.max(np.abs(mlp.params() - ref)) <= 1e-5
+        torch.cuda.synchronize()
+        # FP32 update of O(1) weights by O(lr) steps: a few ulp of the weight
+        assert np.max(np.abs(mlp.params() - ref)) <= 1e-5
 
 
 def test_training_reduces_loss(hqa):

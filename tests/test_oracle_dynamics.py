@@ -223,3 +223,40 @@ def test_replica_driver_equals_single_runs(orc):
             for t in range(2):
                 for k in range(3):
                     assert np.array_equal(runs[t][k][r], one[k]), (r, t, k)
+
+
+def test_table_schedule_hand_value(orc):
+    """The TABLE kind's index conventions (alpha at k = 2m for the kick and 2m + 1 for
+    the drift, beta at m), against three steps worked by hand in exact fractions."""
+    want = {r[0]: [int(r[1]) / int(r[2]), int(r[3]) / int(r[4])]
+            for r in _rows("table_schedule_3step.txt")}
+    ta = np.array([1 / 2, 1 / 4, 1 / 8, 1 / 2, 1 / 4, 1 / 16, 1.0])
+    tb = np.array([1.0, 1 / 2, 1 / 4, 1 / 8])
+    pr = orc.Problem(2, J=np.array([[0.0, -1.0], [-1.0, 0.0]]))
+    phi, p, pbar = orc.md_run(pr, 3, dt=1.0, p0=np.array([1.0, 0.5]), kind=orc.TABLE, M=2,
+                              window=2, table_alpha=ta, table_beta=tb)
+    assert phi.tolist() == want["phi"]
+    assert p.tolist() == want["p"]
+    assert pbar.tolist() == want["phibar"]
+
+
+def test_table_sampled_from_paper_schedule_reproduces_paper_run(orc):
+    """A table holding the paper's polynomials on the half-step grid (alpha at
+    tau = k dt / 2, beta at tau = m dt) gives the PAPER-kind trajectory bitwise."""
+    inst = instances.with_integer_field(instances.er_pm1(60, 0.1, 4), 1, 2)
+    pr = orc.Problem.from_instance(inst)
+    S, dt = 150, 1.0 / 150
+    ta = np.array([orc.schedule(0.5 * k * dt)[0] for k in range(2 * S + 1)])
+    tb = np.array([orc.schedule(m * dt)[1] for m in range(S + 1)])
+    p0 = orc.initial_momenta(5, 0, inst.N)
+    a = orc.md_run(pr, S, dt=dt, p0=p0, window=40)
+    b = orc.md_run(pr, S, dt=dt, p0=p0, window=40, kind=orc.TABLE, table_alpha=ta,
+                   table_beta=tb)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    # a table that differs from the paper's at one half-step index changes the run
+    ta2 = ta.copy()
+    ta2[2 * 70 + 1] *= 1.5
+    c = orc.md_run(pr, S, dt=dt, p0=p0, window=40, kind=orc.TABLE, table_alpha=ta2,
+                   table_beta=tb)
+    assert not np.array_equal(a[0], c[0])

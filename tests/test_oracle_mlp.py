@@ -51,3 +51,35 @@ def test_silent_hidden_layers_closed_form(orc):
     assert np.allclose(g[-2:], sig - y.mean(axis=0), rtol=1e-12)
     # silent layers pass no gradient back: only b3 moves
     assert np.all(g[:-2] == 0.0)
+
+
+def test_adamw_constant_gradient_closed_form(orc):
+    """With the same gradient g at every step the bias-corrected moments are exactly
+    g and g^2, so without decay each step moves w by lr g / (|g| + eps)."""
+    rng = np.random.default_rng(3)
+    w0 = rng.normal(size=300)
+    g = rng.normal(size=300)
+    g[:5] = [0.0, 1e-9, -1e-9, 4.0, -4.0]
+    lr, eps = 1e-2, 1e-6
+    ws = orc.adamw(w0, [g] * 7, lr, 0.9, 0.99, eps, 0.0)
+    for t, w in enumerate(ws, 1):
+        want = w0 - t * lr * g / (np.abs(g) + eps)
+        assert np.max(np.abs(w - want)) <= 1e-12
+
+
+def test_adamw_decay_only_closed_form(orc):
+    """A zero gradient leaves the moments at zero: each step scales w by (1 - lr wd)."""
+    w0 = np.linspace(-2.0, 3.0, 41)
+    lr, wd = 0.05, 0.2
+    ws = orc.adamw(w0, [np.zeros_like(w0)] * 5, lr, 0.9, 0.999, 1e-8, wd)
+    for t, w in enumerate(ws, 1):
+        assert np.allclose(w, w0 * (1 - lr * wd) ** t, rtol=1e-14, atol=0)
+
+
+def test_adamw_first_step_is_sign_like(orc):
+    """Step 1: mhat = g and vhat = g^2 whatever b1, b2; decay acts on the old w."""
+    rng = np.random.default_rng(4)
+    w0, g = rng.normal(size=50), rng.normal(size=50)
+    lr, eps, wd = 3e-3, 1e-8, 0.1
+    (w1,) = orc.adamw(w0, [g], lr, 0.5, 0.75, eps, wd)
+    assert np.allclose(w1, w0 - lr * (g / (np.abs(g) + eps) + wd * w0), rtol=0, atol=1e-15)

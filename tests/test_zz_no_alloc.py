@@ -77,3 +77,68 @@ def test_noalloc_rejects_more_replicas_than_its_scratch_holds(hqa):
     with pytest.raises(hqa.HQAError) as ei:
         ctx.solve_sub_noalloc(spins, frozen, 4, out_s)
     assert ei.value.status == 9     # HQA_ERR_TOO_LARGE
+
+
+def test_noalloc_matches_the_oracle(hqa, orc):
+    """Against the CPU definition of the reduced problem, not only the other entry point."""
+    inst = instances.er_pm1(180, 0.07, 23)
+    ctx = hqa.Context.from_instance(inst)
+    rng = np.random.default_rng(11)
+    R, n = 6, 13
+    spins, frozen = _problem(rng, inst.N, R, n)
+    out_s = torch.empty_like(spins)
+    out_e = torch.empty((R,), dtype=torch.int64, device="cuda")
+    ctx.solve_sub_noalloc(spins, frozen, n, out_s, out_e)
+    ctx.sync()
+    pr = orc.Problem.from_instance(inst)
+    s_h, f_h = spins.cpu().numpy(), frozen.cpu().numpy()
+    for r in range(R):
+        want_s, want_e, _, _ = orc.subsolve(pr, s_h[r], f_h[r])
+        assert np.array_equal(out_s[r].cpu().numpy(), want_s)
+        assert int(out_e[r]) == want_e
+
+
+def test_noalloc_statuses_follow_solve_sub(hqa):
+    """The same request gets the same status from both entry points: a real-valued
+    context (UNSUPPORTED), a batch context (UNSUPPORTED) and n beyond 30 (TOO_LARGE)."""
+    def status(fn, *a):
+        try:
+            fn(*a)
+        except hqa.HQAError as e:
+            return e.status
+        return 0
+
+    real = hqa.Context.from_instance(instances.uniform_sg(64, 3))
+    unit = hqa.Context.from_instance(instances.er_pm1(64, 0.1, 2))
+    batch = hqa.Context.batch([unit])
+    for ctx, n in ((real, 4), (batch, 4), (unit, 31)):
+        R = 8
+        spins = torch.ones((R, ctx.N), dtype=torch.int8, device="cuda")
+        frozen = torch.ones((R, ctx.N), dtype=torch.uint8, device="cuda")
+        out_s = torch.empty_like(spins)
+        out_e = torch.empty((R,), dtype=torch.int64, device="cuda")
+        a = status(ctx.solve_sub, spins, frozen, n)
+        b = status(ctx.solve_sub_noalloc, spins, frozen, n, out_s, out_e)
+        assert a == b != 0
+
+
+def test_noalloc_binding_rejects_wrong_buffers(hqa):
+    """The binding checks the caller's buffers before the library writes through them."""
+    inst = instances.er_pm1(64, 0.1, 8)
+    ctx = hqa.Context.from_instance(inst)
+    R, N = 4, inst.N
+    spins = torch.ones((R, N), dtype=torch.int8, device="cuda")
+    frozen = torch.ones((R, N), dtype=torch.uint8, device="cuda")
+    good_s = torch.empty_like(spins)
+    good_e = torch.empty((R,), dtype=torch.int64, device="cuda")
+    bad = [
+        (spins, frozen, torch.empty((R - 1, N), dtype=torch.int8, device="cuda"), good_e),
+        (spins, frozen, good_s, torch.empty((R,), dtype=torch.int32, device="cuda")),
+        (spins, frozen, good_s, torch.empty((R - 1,), dtype=torch.int64, device="cuda")),
+        (spins, frozen.to(torch.int8), good_s, good_e),
+        (spins, frozen, torch.empty((N, R), dtype=torch.int8, device="cuda").t(), good_e),
+        (spins, frozen, torch.empty((R, N), dtype=torch.int8), good_e),
+    ]
+    for s, f, o, e in bad:
+        with pytest.raises(ValueError):
+            ctx.solve_sub_noalloc(s, f, 4, o, e)
