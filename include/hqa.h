@@ -83,12 +83,20 @@ enum {
     HQA_INIT_GIVEN = 2        /* phi0 / p0 supplied by the caller */
 };
 
-/* Arithmetic of the local-field operand. */
+/* Arithmetic of the local-field operand.  phi and p stay FP32 in every case. */
 enum {
-    HQA_PREC_FP32 = 0,  /* phi operand FP32, FP32 accumulate */
-    HQA_PREC_BF16 = 1,  /* phi operand rounded to BF16, FP32 accumulate; phi, p stay FP32 */
-    HQA_PREC_BF16X2 = 2 /* dense tensor-core path only: phi = hi + lo, both BF16 (about 16
-                           significant bits), two MMAs per k-step, FP32 accumulate */
+    HQA_PREC_FP32 = 0,   /* phi operand FP32, FP32 accumulate (sparse kernels; dense
+                            contexts with HQA_KERNEL_DENSE: an FP32 GEMM on the CUDA cores) */
+    HQA_PREC_BF16 = 1,   /* phi operand rounded to BF16 (8 significant bits), FP32
+                            accumulate; dense: J rounded to BF16 too (exact for +-1) */
+    HQA_PREC_BF16X2 = 2, /* dense tensor-core path only: phi = hi + lo, both BF16 (about 16
+                            significant bits), two K segments, FP32 accumulate */
+    HQA_PREC_FP16 = 3,   /* dense tensor-core path only: phi * 2^6 and J * 2^10 rounded to
+                            FP16 (11 significant bits; exact for +-1 J), FP32 accumulate,
+                            scaled back by 2^-16 */
+    HQA_PREC_FP16X2 = 4  /* dense tensor-core path only: phi * 2^6 = hi + lo, both FP16
+                            (about 22 significant bits), and J split the same way when it
+                            is not exact in FP16; two (exact J) or three K segments */
 };
 
 /* Sparse kernel variants (all compute the same sums, in different orders). */
@@ -97,8 +105,10 @@ enum {
     HQA_KERNEL_SCALAR = 1, /* one replica per lane, neighbour lists streamed from L1/L2 */
     HQA_KERNEL_VECTOR = 2, /* 16-byte gathers per lane, lists in shared memory; needs
                               replicas_per_block >= 4 (FP32) or >= 8 (BF16) */
-    HQA_KERNEL_DENSE = 3,  /* tcgen05 tensor-core GEMM; dense contexts whose couplings
-                              are exact in BF16, BF16 operand only */
+    HQA_KERNEL_DENSE = 3,  /* dense contexts: the field as a GEMM of J and the replicas'
+                              fluxes -- on the tcgen05 tensor cores for the 16-bit
+                              precisions (BF16, BF16X2, FP16, FP16X2), on the CUDA cores
+                              for FP32 */
     HQA_KERNEL_LOWDEG = 4  /* batch contexts whose members have at most 4 couplings per
                               spin and fewer than 2^15 spins: compact lists, operand and
                               state of a work item all in shared memory; replicas_per_block
@@ -145,21 +155,39 @@ void hqa_schedule_default(hqa_schedule* s);
 /* Fills `o` with defaults: FP32, HQA_INIT_PAPER, library-chosen blocking. */
 void hqa_run_opts_default(hqa_run_opts* o);
 
+/* Storage of the coupling operands of a dense context (flags of
+ * hqa_create_dense).  Each copy is also built on first use when absent; a
+ * flag builds it at create instead (so that no later call allocates or
+ * uploads, e.g. before a stream capture).  Couplings of +-1 are exact in
+ * every format. */
+enum {
+    HQA_J_BF16 = 1u << 0, /* BF16 tensor-core operand (always built for the tcgen05 path) */
+    HQA_J_FP16 = 1u << 1, /* FP16 tensor-core operand, J * 2^10 (HQA_PREC_FP16 / FP16X2) */
+    HQA_J_FP32 = 1u << 2, /* FP32 operand of the CUDA-core dense GEMM (HQA_PREC_FP32) */
+    HQA_J_FP8 = 1u << 3   /* FP8 E4M3: not provided (HQA_ERR_UNSUPPORTED).  The kind::f16
+                             MMA needs both operands in the same 16-bit format, and an
+                             FP8 MMA would need phi in FP8 (3 significant bits); widening
+                             an FP8 tile in shared memory would cost more shared-memory
+                             traffic than the L2-resident 16-bit J it replaces */
+};
+
 /* Creates a context from dense couplings (Results Eq. (1)).
  *   N      number of spins, 1..65536
  *   J      host, N*N row-major float; must be symmetric; the diagonal is
  *          ignored (all sums in Eqs. (1), (3) run over j != i)
  *   h      host, N floats, or NULL for h = 0
- *   flags  reserved, pass 0
+ *   flags  0 or an OR of HQA_J_BF16, HQA_J_FP16, HQA_J_FP32
  * The couplings are copied; `*out` owns device copies, among them the
  * tensor-core operand of J.  Precisions on a dense context (hqa_run with
- * HQA_PREC_BF16 / HQA_PREC_BF16X2, the tcgen05 path): BF16 multiplies J and
- * phi rounded to BF16 (J exact for +-1 couplings); BF16X2 splits phi into
- * BF16 hi + lo and, when J is not exact in BF16 (real-valued couplings),
- * J as well: J_hi phi_hi + J_lo phi_hi + J_hi phi_lo, about 16 significant
- * bits of each.  FP32 runs (the CSR kernels) need couplings in {-1, 0, +1}.
- * Errors: INVALID_ARG (N out of range, null J/out), ASYMMETRIC,
- * NONFINITE_INPUT, OOM, CUDA. */
+ * HQA_KERNEL_DENSE, or AUTO with a 16-bit precision): BF16 / FP16 multiply J
+ * and phi rounded to that format (J exact for +-1 couplings); BF16X2 /
+ * FP16X2 split phi into hi + lo and, when J is not exact in the format
+ * (real-valued couplings), J as well: J_hi phi_hi + J_lo phi_hi +
+ * J_hi phi_lo, about 16 (BF16) or 22 (FP16) significant bits of each.  FP32
+ * with HQA_KERNEL_DENSE is an FP32 GEMM on the CUDA cores (any real J); FP32
+ * with the sparse kernels needs couplings in {-1, 0, +1}.
+ * Errors: INVALID_ARG (N out of range, null J/out, unknown flag), ASYMMETRIC,
+ * NONFINITE_INPUT, UNSUPPORTED (HQA_J_FP8), OOM, CUDA. */
 hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t flags,
                             hqa_ctx** out);
 
@@ -172,7 +200,11 @@ hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t 
  *   h        N floats or NULL
  * The pattern and values must be symmetric (entry (i, j) present iff
  * (j, i) present, equal values).  Diagonal entries are dropped.
- * Errors: as hqa_create_dense, plus INVALID_ARG for a malformed CSR. */
+ *   flags  0: the sparse kernels store no coupling values for +-1 couplings
+ *          (a coupling picks the +phi or -phi copy of the operand), so there
+ *          is no storage format to choose.
+ * Errors: as hqa_create_dense, plus INVALID_ARG for a malformed CSR or a
+ * nonzero flags. */
 hqa_status hqa_create_csr(int32_t N, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
                           const float* val, const float* h, uint32_t flags, hqa_ctx** out);
 
@@ -471,7 +503,8 @@ hqa_status hqa_autotune(hqa_ctx* ctx, const hqa_schedule* sched, int32_t replica
  * already prepared by an identical earlier call without capture: launch
  * plans, the schedule table, workspaces and batch work tables.  A call that
  * would have to allocate, upload from the host or synchronise returns
- * HQA_ERR_UNSUPPORTED instead (as does the dense MD, a cooperative launch);
+ * HQA_ERR_UNSUPPORTED instead (the dense tensor-core MD, a cooperative launch,
+ * is recorded as a cooperative kernel node);
  * hqa_capture_end then returns the first failure of the capture and no
  * graph.  hqa_capture_end must follow every successful hqa_capture_begin.
  * The graph replays the same launches with the same pointers and
@@ -498,6 +531,16 @@ void hqa_graph_destroy(hqa_graph* graph);
  * HQA_ERR_TIMEOUT; the context stays usable.  With a set flag the launch
  * is unchanged.  Dense contexts only (UNSUPPORTED otherwise). */
 hqa_status hqa_arm_wait_check(hqa_ctx* ctx, const uint32_t* flag, int64_t step, int64_t limit_ns);
+
+/* Shared-memory bandwidth of the current device in GB/s (no counterpart in the
+ * paper: the measured peak for the roofline of the sparse and batch MD
+ * kernels, whose neighbour gathers are shared-memory loads).  Two CTAs of 1024
+ * threads per SM stream conflict-free 128-bit ld.shared loads over 32 KB;
+ * the best of three timed launches (CUDA events on `stream`, after one
+ * warm-up) is returned in *gbps.  Synchronises `stream`; allocates a small
+ * result buffer.  Errors: INVALID_ARG (null gbps), UNSUPPORTED (during a
+ * capture), CUDA, OOM. */
+hqa_status hqa_probe_smem_bandwidth(double* gbps, void* stream);
 
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */

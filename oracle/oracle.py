@@ -204,6 +204,42 @@ def md_run_replicas(pr: Problem, steps, phi0, p0, dt=None, kind=PAPER, prm=None,
     return phi, p, pbar
 
 
+def md_run_dense_batch(pr: Problem, steps, phi0, p0, dt=None, M=6, hstep=1.0, window=100):
+    """R replicas of a dense problem at once, for long runs at many seeds.
+
+    The same leapfrog as md_run (Methods, "Leapfrog algorithm"; the paper's
+    schedules, Methods "Scheduling functions for MD"), step for step and in the
+    same order, with the coupling sum of all replicas taken as one FP64 matrix
+    product (a library primitive; only the summation order differs from the C
+    routine's loop).  Inputs [R][N]; returns (phi^(S), p^(S-1/2), window mean)."""
+    if pr.J is None:
+        raise ValueError("md_run_dense_batch needs dense couplings")
+    S = int(steps)
+    dt = 1.0 / S if dt is None else float(dt)
+    J = pr.J.copy()
+    np.fill_diagonal(J, 0.0)          # the sums run over j != i
+    phi = np.array(phi0, dtype=np.float64)
+    p = np.array(p0, dtype=np.float64)
+    wsum = np.zeros_like(phi)
+    first_window = max(1, S - int(window) + 1)
+    for m in range(S):
+        alpha, beta = schedule(m * dt)
+        alpha_half, _ = schedule((m + 0.5) * dt)
+        L = phi @ J.T
+        if pr.h is not None:
+            L += 2.0 * pr.h * np.abs(phi)
+        pw = phi.copy()               # phi^(M-1) as repeated products, like the C routine
+        for _ in range(M - 2):
+            pw *= phi
+        F = alpha * M * pw + beta * L
+        c = 0.5 if m == 0 else 1.0
+        p = p - c * hstep * F
+        phi = phi + hstep * alpha_half * p
+        if m + 1 >= first_window:
+            wsum += phi
+    return phi, p, wsum / (S - first_window + 1)
+
+
 def max_threads():
     return int(_load().or_max_threads())
 

@@ -101,7 +101,7 @@ void free_ctx_device(hqa_ctx* c)
                     c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
                     c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat,
                     c->d_tune,    c->d_diag,   c->d_Jcat,  c->d_efx,   c->d_ld,
-                    c->d_ldwork};
+                    c->d_ldwork,  c->d_Jh,     c->d_Jhcat, c->d_Jf32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -256,11 +256,12 @@ hqa_status upload_schedule(hqa_ctx* c, const hqa_schedule* s, double dt, int64_t
     return HQA_OK;
 }
 
+// Operand precisions the sparse (CSR) kernels implement.
+bool sparse_precision(int prec) { return prec == HQA_PREC_FP32 || prec == HQA_PREC_BF16; }
+
 hqa_status check_opts(const hqa_run_opts& o)
 {
-    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16 &&
-        o.precision != HQA_PREC_BF16X2)
-        return HQA_ERR_INVALID_ARG;
+    if (o.precision < HQA_PREC_FP32 || o.precision > HQA_PREC_FP16X2) return HQA_ERR_INVALID_ARG;
     const int rbq = o.replicas_per_block;
     if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
         return HQA_ERR_INVALID_ARG;
@@ -303,6 +304,41 @@ hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& opts, const 
     return hqa_sparse_plan(ctx, RB, o.precision, plan);
 }
 
+// Which dense path a single-context run or field takes: 0 none (the sparse
+// kernels), 1 the tcgen05 GEMM (16-bit precisions), 2 the FP32 CUDA-core GEMM.
+// HQA_KERNEL_DENSE asks for the dense path; AUTO takes it for 16-bit
+// precisions on a dense context, for FP32 only when the couplings are not all
+// +-1 (the sparse kernels need them) or the autotuner chose it.
+hqa_status pick_dense(hqa_ctx* ctx, int32_t R, const hqa_run_opts& o, int* which)
+{
+    const bool tc_prec = hqa_tc_precision(o.precision);
+    bool want = o.kernel == HQA_KERNEL_DENSE;
+    if (o.kernel == HQA_KERNEL_AUTO) {
+        if (tc_prec) want = hqa_dense_md_possible(ctx, R);
+        else if (o.precision == HQA_PREC_FP32 && hqa_simt_possible(ctx)) {
+            const auto it = ctx->tuned.find({R, o.precision});
+            want = !ctx->unit ||
+                   (o.replicas_per_block == 0 && it != ctx->tuned.end() &&
+                    it->second.first == HQA_KERNEL_DENSE);
+        }
+    }
+    *which = 0;
+    if (want) {
+        if (tc_prec) {
+            if (!ctx->dense_tc) return HQA_ERR_UNSUPPORTED;
+            *which = 1;
+        } else if (o.precision == HQA_PREC_FP32) {
+            if (!hqa_simt_possible(ctx)) return HQA_ERR_UNSUPPORTED;
+            *which = 2;
+        } else {
+            return HQA_ERR_UNSUPPORTED;
+        }
+        return HQA_OK;
+    }
+    if (!ctx->unit || !sparse_precision(o.precision)) return HQA_ERR_UNSUPPORTED;
+    return HQA_OK;
+}
+
 // Batch run: one persistent launch over (member, replica block) items, then
 // batched readout and energy.  Kernel: the low-degree one when every member
 // allows it (lists on chip), else the list-streaming one.  Replica blocking:
@@ -317,7 +353,7 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     else hqa_run_opts_default(&o);
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    if (o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR || o.precision == HQA_PREC_BF16X2)
+    if (o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR || !sparse_precision(o.precision))
         return HQA_ERR_UNSUPPORTED;
     // kernel and blocking: the caller's, else the autotuned pair, else the
     // low-degree kernel when every member allows it, else the list-streaming one
@@ -486,7 +522,10 @@ hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t 
 {
     if (!out) return HQA_ERR_INVALID_ARG;
     *out = nullptr;
-    if (N < 1 || N > 65536 || !J || flags != 0) return HQA_ERR_INVALID_ARG;
+    if (N < 1 || N > 65536 || !J) return HQA_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)(HQA_J_BF16 | HQA_J_FP16 | HQA_J_FP32 | HQA_J_FP8))
+        return HQA_ERR_INVALID_ARG;
+    if (flags & HQA_J_FP8) return HQA_ERR_UNSUPPORTED;
     const size_t NN = (size_t)N * N;
     if (!finite_all(J, NN)) return HQA_ERR_NONFINITE_INPUT;
     if (h && !finite_all(h, (size_t)N)) return HQA_ERR_NONFINITE_INPUT;
@@ -512,6 +551,8 @@ hqa_status hqa_create_dense(int32_t N, const float* J, const float* h, uint32_t 
     hqa_status s = create_guarded(c, out);
     if (s != HQA_OK) return s;
     s = hqa_dense_setup(c, J);
+    if (s == HQA_OK && (flags & HQA_J_FP16)) s = hqa_dense_prepare(c, HQA_PREC_FP16);
+    if (s == HQA_OK && (flags & HQA_J_FP32)) s = hqa_simt_prepare(c);
     if (s != HQA_OK) {
         hqa_destroy(c);
         *out = nullptr;
@@ -607,13 +648,10 @@ static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, i
     const bool want_energy = out->energy || out->cut;
     if (want_energy && !ctx->integer) return HQA_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // dense tensor-core path: dense contexts exact in BF16, BF16 operand
-    const bool tc_prec = o.precision == HQA_PREC_BF16 || o.precision == HQA_PREC_BF16X2;
     if (o.kernel == HQA_KERNEL_LOWDEG) return HQA_ERR_UNSUPPORTED;   // batch contexts only
-    const bool dense = o.kernel == HQA_KERNEL_DENSE ||
-                       (o.kernel == HQA_KERNEL_AUTO && tc_prec && hqa_dense_md_possible(ctx, replicas));
-    if (dense && (!ctx->dense_tc || !tc_prec)) return HQA_ERR_UNSUPPORTED;
-    if (!dense && (!ctx->unit || o.precision == HQA_PREC_BF16X2)) return HQA_ERR_UNSUPPORTED;
+    int dense = 0;   // 1: tcgen05 GEMM, 2: FP32 CUDA-core GEMM
+    s = pick_dense(ctx, replicas, o, &dense);
+    if (s != HQA_OK) return s;
 
     const SparsePlan* plan = nullptr;
     if (!dense) {
@@ -643,10 +681,12 @@ static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, i
     int8_t* spins = out->spins;
     if (tmp_spins) spins = reinterpret_cast<int8_t*>(ws);
 
-    if (dense)
+    if (dense == 1)
         s = hqa_dense_launch_md(ctx, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
-                                o.phi0, o.p0, sched->M, out->phi, out->p, phibar,
-                                o.precision == HQA_PREC_BF16X2, st);
+                                o.phi0, o.p0, sched->M, out->phi, out->p, phibar, o.precision, st);
+    else if (dense == 2)
+        s = hqa_simt_launch_md(ctx, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
+                               o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
     else if (plan->vec)
         s = hqa_vec_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
                               o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
@@ -686,12 +726,11 @@ static hqa_status local_field_impl(hqa_ctx* ctx, int32_t replicas, const float* 
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (o.kernel == HQA_KERNEL_DENSE || (o.kernel == HQA_KERNEL_AUTO && ctx->dense_tc &&
-                                         o.precision == HQA_PREC_BF16)) {
-        if (!ctx->dense_tc || o.precision != HQA_PREC_BF16) return HQA_ERR_UNSUPPORTED;
-        return hqa_dense_field(ctx, replicas, phi, L, st);
-    }
-    if (!ctx->unit || o.precision == HQA_PREC_BF16X2) return HQA_ERR_UNSUPPORTED;
+    int dense = 0;
+    s = pick_dense(ctx, replicas, o, &dense);
+    if (s != HQA_OK) return s;
+    if (dense == 1) return hqa_dense_field(ctx, replicas, phi, L, o.precision, st);
+    if (dense == 2) return hqa_simt_field(ctx, replicas, phi, L, st);
     const SparsePlan* plan = nullptr;
     s = choose_plan(ctx, replicas, o, &plan);
     if (s != HQA_OK) return s;
@@ -772,12 +811,24 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
     else hqa_run_opts_default(&o);
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    const bool tc_prec = o.precision == HQA_PREC_BF16 || o.precision == HQA_PREC_BF16X2;
-    if (o.kernel == HQA_KERNEL_DENSE ||
-        (o.kernel == HQA_KERNEL_AUTO && tc_prec && hqa_dense_md_possible(ctx, replicas))) {
+    int dense = 0;
+    s = pick_dense(ctx, replicas, o, &dense);
+    if (s != HQA_OK) return s;
+    if (dense == 2) {
+        out->kernel = HQA_KERNEL_DENSE;
+        out->replicas_per_block = 128;
+        out->blocks = ((replicas + 127) / 128) * ((ctx->N + 127) / 128);
+        out->threads = 256;
+        out->smem_bytes = 0;
+        out->chunks = 1;
+        out->pad_ratio = (double)out->blocks * 128 * 128 / ((double)ctx->N * replicas);
+        out->conflict_ratio = 1.0;
+        out->balance = 1.0;
+        return HQA_OK;
+    }
+    if (dense == 1) {
         int nh = 0, grid = 0;
-        if (!ctx->dense_tc || !tc_prec) return HQA_ERR_UNSUPPORTED;
-        const int C = hqa_dense_md_chunks(ctx, replicas, o.precision == HQA_PREC_BF16X2);
+        const int C = hqa_dense_md_chunks(ctx, replicas, o.precision);
         const int Rc = (replicas + C - 1) / C;
         if (!hqa_dense_md_geometry(ctx, Rc, &nh, &grid)) return HQA_ERR_UNSUPPORTED;
         out->kernel = HQA_KERNEL_DENSE;
@@ -791,7 +842,6 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
         out->balance = 1.0;
         return HQA_OK;
     }
-    if (!ctx->unit || o.precision == HQA_PREC_BF16X2) return HQA_ERR_UNSUPPORTED;
     const SparsePlan* plan = nullptr;
     s = choose_plan(ctx, replicas, o, &plan);
     if (s != HQA_OK) return s;

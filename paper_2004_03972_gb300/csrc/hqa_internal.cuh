@@ -185,6 +185,17 @@ struct hqa_ctx {
     uint64_t wait_ns = 0;
     void* d_Jcat = nullptr;        // [Mpad][3 Mpad] BF16 (non-exact J only)
     CUtensorMap tmJ3;
+    // FP16 tensor-core operands (built on first use): J scaled by 2^10 and rounded
+    // to FP16, and the split [J_hi | J_lo | J_hi] when that rounding is not exact
+    bool dense_f16 = false;
+    bool dense_exact16 = false;
+    void* d_Jh = nullptr;          // [Mpad][Mpad] FP16
+    void* d_Jhcat = nullptr;       // [Mpad][3 Mpad] FP16 (J not exact in FP16 only)
+    CUtensorMap tmJh;
+    CUtensorMap tmJh3;
+    // plain FP32 dense path (CUDA cores): J in FP32, [Npad32][Npad32], built on first use
+    float* d_Jf32 = nullptr;
+    int Npad32 = 0;
 };
 
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;
@@ -244,14 +255,26 @@ hqa_status hqa_sparse_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t
 
 // dense_md.cu
 hqa_status hqa_dense_setup(hqa_ctx* ctx, const float* J);
-hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, cudaStream_t st);
+hqa_status hqa_dense_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, int prec,
+                           cudaStream_t st);
 bool hqa_dense_md_possible(const hqa_ctx* ctx, int32_t R);
 int hqa_dense_md_geometry(const hqa_ctx* ctx, int32_t R, int* nh, int* grid);
-int hqa_dense_md_chunks(const hqa_ctx* ctx, int32_t R, bool split);
+int hqa_dense_md_chunks(const hqa_ctx* ctx, int32_t R, int prec);
+// precision: HQA_PREC_BF16, _BF16X2, _FP16 or _FP16X2
+bool hqa_tc_precision(int prec);
+hqa_status hqa_dense_prepare(hqa_ctx* ctx, int prec);
 hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
                                int32_t R, uint64_t seed, int init, const float* phi0,
                                const float* p0, int M, float* phi_out, float* p_out,
-                               float* phibar_out, bool split, cudaStream_t st);
+                               float* phibar_out, int prec, cudaStream_t st);
+// dense_simt.cu: the plain FP32 dense path on the CUDA cores
+bool hqa_simt_possible(const hqa_ctx* ctx);
+hqa_status hqa_simt_prepare(hqa_ctx* ctx);
+hqa_status hqa_simt_field(hqa_ctx* ctx, int32_t R, const float* phi, float* L, cudaStream_t st);
+hqa_status hqa_simt_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S, int32_t W,
+                              int32_t R, uint64_t seed, int init, const float* phi0,
+                              const float* p0, int M, float* phi_out, float* p_out,
+                              float* phibar_out, cudaStream_t st);
 
 // readout.cu
 hqa_status hqa_launch_readout_batch(hqa_ctx* batch, int32_t R, const float* phibar, int32_t n,

@@ -117,7 +117,8 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate (kind::f16)
+// D[tmem] (+)= A[smem] * B[smem]^T, 16-bit inputs (both BF16 or both FP16, as
+// the instruction descriptor says), FP32 accumulate (kind::f16)
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate)
 {
@@ -183,6 +184,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4)                 // D format F32
          | (1u << 7)                 // A format BF16
          | (1u << 10)                // B format BF16
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f16: D F32, A/B FP16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4)                 // D format F32
+         | (0u << 7)                 // A format F16
+         | (0u << 10)                // B format F16
          | ((uint32_t)(N >> 3) << 17)
          | ((uint32_t)(M >> 4) << 24);
 }

@@ -6,7 +6,8 @@
 // vectorised sparse kernel at the blockings that fill a 16-byte vector, the
 // persistent batch kernels (list-streaming at 1..32 replicas per block, the
 // low-degree one at 1, 2, 4 where every member allows it), and the dense
-// tensor-core kernel (dense contexts in BF16 / BF16X2).  Each one
+// GEMM kernels (dense contexts: tcgen05 for the 16-bit precisions, the FP32
+// CUDA-core GEMM for FP32).  Each one
 // runs a short probe anneal (probe_steps leapfrog steps, dt = 1/probe_steps,
 // init PAPER) once untimed (plan build, caches) and then three times between
 // CUDA events on the caller's stream; the figure kept is the mean time per
@@ -27,12 +28,16 @@ std::vector<Cand> candidates(const hqa_ctx* ctx, int prec)
 {
     std::vector<Cand> c;
     const int rbs[6] = {1, 2, 4, 8, 16, 32};
-    if (!ctx->is_batch && ctx->dense_tc && prec != HQA_PREC_FP32) {
+    if (!ctx->is_batch && ctx->dense_tc && hqa_tc_precision(prec)) {
         c.push_back({HQA_KERNEL_DENSE, 0});
         return c;
     }
+    // FP32 on a dense context: the CUDA-core GEMM, and the sparse kernels
+    // when the couplings are all +-1
+    if (prec == HQA_PREC_FP32 && hqa_simt_possible(ctx)) c.push_back({HQA_KERNEL_DENSE, 0});
+    if (!ctx->unit || (prec != HQA_PREC_FP32 && prec != HQA_PREC_BF16)) return c;
     for (int rb : rbs) c.push_back({HQA_KERNEL_SCALAR, rb});
-    if (ctx->is_batch && hqa_lowdeg_eligible(ctx) && prec != HQA_PREC_BF16X2)
+    if (ctx->is_batch && hqa_lowdeg_eligible(ctx))
         for (int rb : {1, 2, 4}) c.push_back({HQA_KERNEL_LOWDEG, rb});
     if (!ctx->is_batch) {
         const int V = prec == HQA_PREC_BF16 ? 8 : 4;
@@ -56,9 +61,7 @@ extern "C" hqa_status hqa_autotune(hqa_ctx* ctx, const hqa_schedule* sched, int3
     hqa_run_opts o;
     if (opts) o = *opts;
     else hqa_run_opts_default(&o);
-    if (o.precision != HQA_PREC_FP32 && o.precision != HQA_PREC_BF16 &&
-        o.precision != HQA_PREC_BF16X2)
-        return HQA_ERR_INVALID_ARG;
+    if (o.precision < HQA_PREC_FP32 || o.precision > HQA_PREC_FP16X2) return HQA_ERR_INVALID_ARG;
     o.init = HQA_INIT_PAPER;
     o.phi0 = nullptr;
     o.p0 = nullptr;

@@ -23,7 +23,8 @@ STATUS_NAMES = {
 }
 SCHED_PAPER, SCHED_LINEAR_GAMMA, SCHED_TABLE = 0, 1, 2
 INIT_PAPER, INIT_RANDOM_FLUX, INIT_GIVEN = 0, 1, 2
-PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16, PREC_FP16X2 = 0, 1, 2, 3, 4
+J_BF16, J_FP16, J_FP32, J_FP8 = 1, 2, 4, 8
 KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_DENSE, KERNEL_LOWDEG = 0, 1, 2, 3, 4
 
 # every symbol include/hqa.h declares
@@ -36,7 +37,7 @@ EXPORTS = (
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
     "hqa_autotune", "hqa_hmd", "hqa_energy_f64", "hqa_run_trace", "hqa_solve_sub_tabu",
-    "hqa_arm_wait_check",
+    "hqa_arm_wait_check", "hqa_probe_smem_bandwidth",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -140,6 +141,8 @@ def lib() -> C.CDLL:
                                        C.POINTER(RunOpts), C.POINTER(TuneEntry), i32,
                                        C.POINTER(i32), vp]
             L.hqa_autotune.restype = C.c_int
+            L.hqa_probe_smem_bandwidth.argtypes = [C.POINTER(C.c_double), vp]
+            L.hqa_probe_smem_bandwidth.restype = C.c_int
             L.hqa_arm_wait_check.argtypes = [vp, vp, i64, i64]
             L.hqa_arm_wait_check.restype = C.c_int
             L.hqa_solve_sub_tabu.argtypes = [vp, i32, vp, vp, i32, i32, i32, vp, vp, vp]
@@ -198,6 +201,14 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def smem_bandwidth_probe(stream=None) -> float:
+    """hqa_probe_smem_bandwidth: measured shared-memory bandwidth of the current GPU, GB/s."""
+    v = C.c_double()
+    _check(lib().hqa_probe_smem_bandwidth(C.byref(v), _stream_ptr(stream)),
+           "hqa_probe_smem_bandwidth")
+    return v.value
+
+
 class Context:
     """Owns an hqa_ctx (device copies of the couplings)."""
 
@@ -227,13 +238,15 @@ class Context:
         return views
 
     @classmethod
-    def from_dense(cls, J, h=None):
+    def from_dense(cls, J, h=None, flags=0):
+        """hqa_create_dense; ``flags`` (J_BF16 | J_FP16 | J_FP32) builds those coupling
+        operands at create instead of on first use."""
         J = np.ascontiguousarray(J, dtype=np.float32)
         N = J.shape[0]
         hh = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
         out = C.c_void_p()
         _check(lib().hqa_create_dense(N, J.ctypes.data, None if hh is None else hh.ctypes.data,
-                                      0, C.byref(out)), "hqa_create_dense")
+                                      int(flags), C.byref(out)), "hqa_create_dense")
         return cls(out, N)
 
     @classmethod
@@ -249,9 +262,9 @@ class Context:
         return cls(out, int(N))
 
     @classmethod
-    def from_instance(cls, inst):
+    def from_instance(cls, inst, flags=0):
         if inst.dense is not None:
-            return cls.from_dense(inst.dense, inst.h)
+            return cls.from_dense(inst.dense, inst.h, flags)
         return cls.from_csr(inst.N, inst.row_ptr, inst.col, inst.val, inst.h)
 
     def info(self):

@@ -86,7 +86,9 @@ def test_enum_constants_match_header(tmp_path):
         ("SCHED_TABLE", hqa.SCHED_TABLE), ("INIT_PAPER", hqa.INIT_PAPER),
         ("INIT_RANDOM_FLUX", hqa.INIT_RANDOM_FLUX), ("INIT_GIVEN", hqa.INIT_GIVEN),
         ("PREC_FP32", hqa.PREC_FP32), ("PREC_BF16", hqa.PREC_BF16),
-        ("PREC_BF16X2", hqa.PREC_BF16X2), ("KERNEL_AUTO", hqa.KERNEL_AUTO),
+        ("PREC_BF16X2", hqa.PREC_BF16X2), ("PREC_FP16", hqa.PREC_FP16),
+        ("PREC_FP16X2", hqa.PREC_FP16X2), ("J_BF16", hqa.J_BF16), ("J_FP16", hqa.J_FP16),
+        ("J_FP32", hqa.J_FP32), ("J_FP8", hqa.J_FP8), ("KERNEL_AUTO", hqa.KERNEL_AUTO),
         ("KERNEL_SCALAR", hqa.KERNEL_SCALAR), ("KERNEL_VECTOR", hqa.KERNEL_VECTOR),
         ("KERNEL_DENSE", hqa.KERNEL_DENSE), ("KERNEL_LOWDEG", hqa.KERNEL_LOWDEG),
         ("MLP_IN", hqa.MLP_IN), ("MLP_HIDDEN", hqa.MLP_HIDDEN), ("MLP_OUT", hqa.MLP_OUT),

@@ -112,20 +112,30 @@ def test_unprepared_capture_fails_cleanly(hqa):
     assert torch.isfinite(out["phi"]).all()
 
 
-def test_dense_md_is_not_captured(hqa):
+@pytest.mark.parametrize("prec", [0, 1, 3, 4])
+def test_dense_md_graph_replay(hqa, prec):
+    """The dense MD (the persistent tcgen05 kernel, recorded as a cooperative kernel
+    node, or the per-step FP32 CUDA-core launches) replays from a graph with the
+    results of an eager run, bitwise."""
     inst = instances.sk_pm1(256, 7)
     ctx = hqa.Context.from_instance(inst)
     R, S = 128, 50
     st = torch.cuda.Stream()
+    kw = dict(precision=prec, kernel=hqa.KERNEL_DENSE, stream=st, seed=3)
+    ref = ctx.run(S, R, **kw, outputs=("phi", "p", "phibar", "cut"))
     out = _outs(R, inst.N, R)
-    ctx.run(S, R, precision=hqa.PREC_BF16, out=out, stream=st)
+    ctx.run(S, R, **kw, out=out)                   # prepares plan, table and workspaces
     st.synchronize()
-    with pytest.raises(hqa.HQAError) as ei:
-        with hqa.capture(st):
-            ctx.run(S, R, precision=hqa.PREC_BF16, out=out, stream=st)
-    assert ei.value.status == 6
-    ctx.run(S, R, precision=hqa.PREC_BF16, out=out, stream=st)
+    with hqa.capture(st) as cap:
+        ctx.run(S, R, **kw, out=out)
+    for v in out.values():
+        v.zero_()
+    for _ in range(2):
+        cap.graph.launch(st)
     st.synchronize()
+    ctx.sync(st)
+    for k in ("phi", "p", "phibar", "cut"):
+        assert torch.equal(out[k], ref[k]), k
 
 
 @pytest.mark.parametrize("prec", [0, 1])

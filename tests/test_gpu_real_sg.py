@@ -39,6 +39,20 @@ def hqa():
     return H
 
 
+def test_field_fp32(hqa, orc):
+    """Real J on the CUDA-core FP32 GEMM: within 1e-5 of the conditioning scale."""
+    inst = instances.uniform_sg(700, 6)
+    ctx = hqa.Context.from_instance(inst)
+    phi = np.random.default_rng(4).uniform(-1.5, 1.5, size=(33, inst.N)).astype(np.float32)
+    L = ctx.local_field(torch.from_numpy(phi).cuda(), precision=hqa.PREC_FP32,
+                        kernel=hqa.KERNEL_DENSE).cpu().numpy().astype(np.float64)
+    ctx.sync()
+    x = phi.astype(np.float64)
+    ref = x @ inst.dense.T + 2 * inst.h * np.abs(x)
+    scale = np.abs(ref) + np.abs(x) @ np.abs(inst.dense).T + 2 * np.abs(inst.h) * np.abs(x)
+    assert np.max(np.abs(L - ref) / scale) <= 1e-5
+
+
 def test_field_bf16(hqa, orc):
     inst = instances.uniform_sg(300, 5)
     ctx = hqa.Context.from_instance(inst)
@@ -61,9 +75,17 @@ def _close(gpu, ref, tol, scale=None):
     return np.max(np.abs(gpu - ref)) <= tol * s
 
 
+# FP32 (the CUDA-core GEMM) and the FP16 forms, measured on GB300 over 8 replicas
+# (phi, p) at N = 300, 1000: FP32 3.5e-6, 8.0e-6; FP16X2 1.3e-5, 9.8e-5; FP16 1.7e-3,
+# 8.6e-3.  Bounds: FP32 1e-5 (N <= 300), 3e-5 stated at N = 1000 (FP32 rounding grown
+# by the same instability as in the dense SK tests); FP16X2 as BF16X2; FP16 1e-2 at
+# N <= 300, 2e-2 stated at N = 1000.
 @pytest.mark.parametrize("N,R,prec,tol", [
     (100, 8, 1, 1e-2), (300, 64, 1, 2.5e-2), (1000, 130, 1, 1e-1),
-    (100, 8, 2, 1e-4), (300, 64, 2, 1e-4), (1000, 130, 2, 3e-4)])
+    (100, 8, 2, 1e-4), (300, 64, 2, 1e-4), (1000, 130, 2, 3e-4),
+    (100, 8, 4, 1e-4), (300, 64, 4, 1e-4), (1000, 130, 4, 3e-4),
+    (100, 8, 0, 1e-5), (300, 64, 0, 1e-5), (1000, 130, 0, 3e-5),
+    (100, 8, 3, 1e-2), (300, 64, 3, 1e-2), (1000, 130, 3, 2e-2)])
 def test_states_after_100_steps(hqa, orc, N, R, prec, tol):
     inst = instances.uniform_sg(N, 7 + N)
     ctx = hqa.Context.from_instance(inst)
@@ -89,9 +111,9 @@ def sg10k(hqa, orc):
     return hqa.Context.from_instance(inst), ref, inst
 
 
-@pytest.mark.parametrize("N", [1000, 10000])
-def test_split_field(hqa, sg10k, N):
-    """The BF16X2 field on the tensor cores, recovered from one leapfrog step from a
+@pytest.mark.parametrize("N,prec", [(1000, 2), (10000, 2), (1000, 4), (10000, 4)])
+def test_split_field(hqa, sg10k, N, prec):
+    """The split (BF16X2, FP16X2) field on the tensor cores, recovered from one leapfrog step from a
     given phi(0) with p(0) = 0: p(1/2) = -F(phi(0), 0) / 2 (Methods, "Leapfrog
     algorithm"), so L = (-2 p(1/2) - alpha M phi^(M-1)) / beta - 2 h |phi|."""
     from oracle import oracle as orc
@@ -102,7 +124,7 @@ def test_split_field(hqa, sg10k, N):
         ctx = hqa.Context.from_instance(inst)
     R = 16
     phi0 = np.random.default_rng(5).uniform(-1.5, 1.5, size=(R, N)).astype(np.float32)
-    out = ctx.run(1, R, seed=0, dt=1e-4, precision=hqa.PREC_BF16X2, kernel=hqa.KERNEL_DENSE,
+    out = ctx.run(1, R, seed=0, dt=1e-4, precision=prec, kernel=hqa.KERNEL_DENSE,
                   init=hqa.INIT_GIVEN, phi0=torch.from_numpy(phi0).cuda(),
                   p0=torch.zeros((R, N), dtype=torch.float32, device="cuda"), outputs=("p",))
     ctx.sync()
@@ -116,7 +138,7 @@ def test_split_field(hqa, sg10k, N):
     assert np.max(np.abs(L - ref) / scale) <= np.sqrt(K) * 2.0 ** -24 + 2.0 ** -20
 
 
-@pytest.mark.parametrize("prec,tol", [(2, 3.5e-3), (1, 2.5e-2)])
+@pytest.mark.parametrize("prec,tol", [(2, 3.5e-3), (4, 3.5e-3), (1, 2.5e-2)])
 def test_states_n10000(hqa, sg10k, prec, tol):
     ctx, ref, _ = sg10k
     assert ctx.plan(8, precision=prec)["kernel"] == hqa.KERNEL_DENSE

@@ -260,3 +260,19 @@ def test_table_sampled_from_paper_schedule_reproduces_paper_run(orc):
     c = orc.md_run(pr, S, dt=dt, p0=p0, window=40, kind=orc.TABLE, table_alpha=ta2,
                    table_beta=tb)
     assert not np.array_equal(a[0], c[0])
+
+
+@pytest.mark.parametrize("field", [False, True])
+def test_dense_batch_oracle_equals_per_replica_oracle(orc, field):
+    """The batched dense form (one FP64 matrix product per step for all replicas)
+    follows the per-replica C routine to rounding: same schedule indices, half
+    first kick, window and field term."""
+    inst = instances.uniform_sg(90, 3) if field else instances.sk_pm1(90, 3)
+    pr = orc.Problem.from_instance(inst)
+    R, S = 5, 300
+    p0 = np.stack([orc.initial_momenta(9, r, inst.N) for r in range(R)])
+    phi0 = np.stack([orc.initial_flux_random(9, r, inst.N) for r in range(R)])
+    a = orc.md_run_dense_batch(pr, S, phi0, p0, dt=1.0 / 400, window=30)
+    b = orc.md_run_replicas(pr, S, phi0, p0, dt=1.0 / 400, window=30)
+    for x, y in zip(a, b):
+        assert np.max(np.abs(x - y)) <= 1e-9 * max(1.0, np.max(np.abs(y)))
