@@ -283,8 +283,9 @@ hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& opts, const 
         }
     }
     int RB = o.replicas_per_block;
+    int rb_scalar = RB;   // the scalar kernel's blocking if the vectorised one is not used
     if (RB == 0) {
-        RB = hqa_sparse_pick_rb(ctx, R, o.precision);
+        RB = rb_scalar = hqa_sparse_pick_rb(ctx, R, o.precision);
         // the vectorised kernel needs a full 16-byte vector of replicas per lane
         const int V = o.precision == HQA_PREC_BF16 ? 8 : 4;
         if (o.kernel != HQA_KERNEL_SCALAR && RB < V && RB > 0 && R >= V) RB = V;
@@ -300,6 +301,7 @@ hqa_status choose_plan(hqa_ctx* ctx, int32_t R, const hqa_run_opts& opts, const 
         }
     }
     if (o.kernel == HQA_KERNEL_VECTOR) return HQA_ERR_UNSUPPORTED;
+    if (rb_scalar > 0) RB = rb_scalar;   // the vector width was only for the vectorised kernel
     if (hqa_sparse_smem_bytes(ctx, RB, o.precision) > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     return hqa_sparse_plan(ctx, RB, o.precision, plan);
 }

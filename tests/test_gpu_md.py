@@ -295,3 +295,29 @@ def test_resume_is_bitwise(hqa, kernel, prec, name):
     b = ctx.run(S, R, init=hqa.INIT_GIVEN, phi0=a["phi"], p0=a["p"], start_step=S, **kw)
     ctx.sync()
     assert torch.equal(full["phi"], b["phi"]) and torch.equal(full["p"], b["p"])
+
+
+@pytest.fixture(scope="module")
+def er20k(orc):
+    """The largest size of the surrogate-gated workload: ER N = 20000, mean degree 8, +-1,
+    with the oracle's 100-step states of replicas 0 and 255 (dt = 1e-4)."""
+    inst = instances.er_mean_degree_pm1(20000, 8.0, 21500)
+    pr = orc.Problem.from_instance(inst)
+    ref = {r: orc.md_run(pr, 100, dt=1e-4, p0=orc.initial_momenta(13, r, inst.N))
+           for r in (0, 255)}
+    return inst, ref
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 1e-2)])
+def test_states_after_100_steps_er20000(hqa, er20k, prec, tol):
+    """States at the size and replica count the surrogate-gated workload runs (256
+    replicas, the launch shape the library picks for it)."""
+    inst, ref = er20k
+    ctx = hqa.Context.from_instance(inst)
+    out = ctx.run(100, 256, seed=13, dt=1e-4, precision=prec, outputs=("phi", "p", "phibar"))
+    ctx.sync()
+    for r, (ophi, op, opbar) in ref.items():
+        assert _states_close(out["phi"][r].cpu().numpy(), ophi, tol)
+        assert _states_close(out["p"][r].cpu().numpy(), op, tol, scale=1.0)
+        assert _states_close(out["phibar"][r].cpu().numpy(), opbar, tol,
+                             scale=np.max(np.abs(ophi)))
