@@ -464,8 +464,9 @@ def measure(name, args, hqa, torch, timer, dev, ws, rank, headline):
     parity = cfg["parity"]
     main_plain = cfg["variants"][0][4]
     eligible = [k for k in variants if eq[k]["holds"] and parity[k][1]
-                and variants[k]["plain"] == main_plain]
-    head = min(eligible, key=lambda k: np.mean(variants[k]["t_pipe"]))
+                and variants[k]["plain"] == main_plain and not variants[k]["one_at_a_time"]]
+    head = max(eligible, key=lambda k: variants[k]["su_step"] * variants[k]["steps"]
+               / sum(variants[k]["t_pipe"]))
     hv = variants[head]
 
     # the MD kernel alone (roofline), on the stream it is launched on

@@ -109,10 +109,17 @@ enum {
                               fluxes -- on the tcgen05 tensor cores for the 16-bit
                               precisions (BF16, BF16X2, FP16, FP16X2), on the CUDA cores
                               for FP32 */
-    HQA_KERNEL_LOWDEG = 4  /* batch contexts whose members have at most 4 couplings per
+    HQA_KERNEL_LOWDEG = 4, /* batch contexts whose members have at most 4 couplings per
                               spin and fewer than 2^15 spins: compact lists, operand and
                               state of a work item all in shared memory; replicas_per_block
                               1, 2 or 4.  AUTO picks it for such batches */
+    HQA_KERNEL_STREAM = 5  /* single contexts with couplings in {-1, 0, +1}, FP32 or BF16:
+                              the operand and state in global memory (L2-resident at the
+                              sizes it serves), one persistent cooperative grid with a
+                              bounded-wait barrier per step.  For instances whose operand
+                              does not fit in one SM's shared memory; AUTO takes it when
+                              the resident kernels cannot run (HQA_ERR_TOO_LARGE) or the
+                              autotuner chose it */
 };
 
 typedef struct {

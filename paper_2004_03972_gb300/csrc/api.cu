@@ -265,7 +265,7 @@ hqa_status check_opts(const hqa_run_opts& o)
     const int rbq = o.replicas_per_block;
     if (rbq != 0 && rbq != 1 && rbq != 2 && rbq != 4 && rbq != 8 && rbq != 16 && rbq != 32)
         return HQA_ERR_INVALID_ARG;
-    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_LOWDEG) return HQA_ERR_INVALID_ARG;
+    if (o.kernel < HQA_KERNEL_AUTO || o.kernel > HQA_KERNEL_STREAM) return HQA_ERR_INVALID_ARG;
     return HQA_OK;
 }
 
@@ -341,6 +341,31 @@ hqa_status pick_dense(hqa_ctx* ctx, int32_t R, const hqa_run_opts& o, int* which
     return HQA_OK;
 }
 
+// Sparse launch for a single context: the streaming kernel when asked for,
+// when the autotuner chose it, or (AUTO) when no resident plan fits; else the
+// resident plan (*plan).
+hqa_status pick_sparse(hqa_ctx* ctx, int32_t R, const hqa_run_opts& o, const SparsePlan** plan,
+                       bool* stream)
+{
+    *stream = false;
+    *plan = nullptr;
+    bool want = o.kernel == HQA_KERNEL_STREAM;
+    if (o.kernel == HQA_KERNEL_AUTO && o.replicas_per_block == 0) {
+        const auto it = ctx->tuned.find({R, o.precision});
+        want = it != ctx->tuned.end() && it->second.first == HQA_KERNEL_STREAM;
+    }
+    if (!want) {
+        hqa_status s = choose_plan(ctx, R, o, plan);
+        if (s != HQA_ERR_TOO_LARGE || o.kernel != HQA_KERNEL_AUTO ||
+            !hqa_stream_supported(ctx, o.precision))
+            return s;
+    }
+    if (!hqa_stream_supported(ctx, o.precision)) return HQA_ERR_UNSUPPORTED;
+    *plan = nullptr;
+    *stream = true;
+    return HQA_OK;
+}
+
 // Batch run: one persistent launch over (member, replica block) items, then
 // batched readout and energy.  Kernel: the low-degree one when every member
 // allows it (lists on chip), else the list-streaming one.  Replica blocking:
@@ -355,7 +380,8 @@ hqa_status run_batch(hqa_ctx* ctx, const hqa_schedule* sched, double dt, int64_t
     else hqa_run_opts_default(&o);
     hqa_status s = check_opts(o);
     if (s != HQA_OK) return s;
-    if (o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR || !sparse_precision(o.precision))
+    if (o.kernel == HQA_KERNEL_DENSE || o.kernel == HQA_KERNEL_VECTOR ||
+        o.kernel == HQA_KERNEL_STREAM || !sparse_precision(o.precision))
         return HQA_ERR_UNSUPPORTED;
     // kernel and blocking: the caller's, else the autotuned pair, else the
     // low-degree kernel when every member allows it, else the list-streaming one
@@ -656,8 +682,9 @@ static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, i
     if (s != HQA_OK) return s;
 
     const SparsePlan* plan = nullptr;
+    bool streaming = false;
     if (!dense) {
-        s = choose_plan(ctx, replicas, o, &plan);
+        s = pick_sparse(ctx, replicas, o, &plan, &streaming);
         if (s != HQA_OK) return s;
     }
     s = upload_schedule(ctx, sched, dt, steps, o.start_step);
@@ -689,6 +716,10 @@ static hqa_status run_impl(hqa_ctx* ctx, const hqa_schedule* sched, double dt, i
     else if (dense == 2)
         s = hqa_simt_launch_md(ctx, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
                                o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
+    else if (streaming)
+        s = hqa_stream_launch_md(ctx, o.precision, ctx->d_sched, steps, sched->window, replicas,
+                                 seed, o.init, o.phi0, o.p0, sched->M, out->phi, out->p, phibar,
+                                 st);
     else if (plan->vec)
         s = hqa_vec_launch_md(ctx, plan, ctx->d_sched, steps, sched->window, replicas, seed, o.init,
                               o.phi0, o.p0, sched->M, out->phi, out->p, phibar, st);
@@ -734,8 +765,10 @@ static hqa_status local_field_impl(hqa_ctx* ctx, int32_t replicas, const float* 
     if (dense == 1) return hqa_dense_field(ctx, replicas, phi, L, o.precision, st);
     if (dense == 2) return hqa_simt_field(ctx, replicas, phi, L, st);
     const SparsePlan* plan = nullptr;
-    s = choose_plan(ctx, replicas, o, &plan);
+    bool streaming = false;
+    s = pick_sparse(ctx, replicas, o, &plan, &streaming);
     if (s != HQA_OK) return s;
+    if (streaming) return hqa_stream_field(ctx, o.precision, replicas, phi, L, st);
     if (plan->vec) return hqa_vec_launch_field(ctx, plan, replicas, phi, L, st);
     return hqa_sparse_launch_field(ctx, plan, replicas, phi, L, st);
 }
@@ -836,7 +869,7 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
         out->kernel = HQA_KERNEL_DENSE;
         out->replicas_per_block = 2 * nh;
         out->blocks = grid;
-        out->threads = 320;
+        out->threads = 448;         // TMA warp, MMA warp, 12 epilogue warps
         out->smem_bytes = 0;
         out->chunks = C;
         out->pad_ratio = (double)C * grid * 128 * 2 * nh / ((double)ctx->N * replicas);
@@ -845,8 +878,22 @@ hqa_status hqa_plan_query(hqa_ctx* ctx, int32_t replicas, const hqa_run_opts* op
         return HQA_OK;
     }
     const SparsePlan* plan = nullptr;
-    s = choose_plan(ctx, replicas, o, &plan);
+    bool stream = false;
+    s = pick_sparse(ctx, replicas, o, &plan, &stream);
     if (s != HQA_OK) return s;
+    if (stream) {
+        const int V = o.precision == HQA_PREC_BF16 ? 8 : 4;
+        out->kernel = HQA_KERNEL_STREAM;
+        out->replicas_per_block = V;
+        out->blocks = 0;            // persistent: as many CTAs as are co-resident
+        out->threads = 256;
+        out->smem_bytes = 0;
+        out->chunks = 1;
+        out->pad_ratio = (double)((replicas + V - 1) / V * V) / replicas;
+        out->conflict_ratio = 1.0;
+        out->balance = 1.0;
+        return HQA_OK;
+    }
     out->kernel = plan->vec ? HQA_KERNEL_VECTOR : HQA_KERNEL_SCALAR;
     out->chunks = 1;
     out->replicas_per_block = plan->RB;

@@ -49,14 +49,17 @@ __device__ __forceinline__ float from16(uint16_t u)
 //             epilogue of (m-1, h) (arrival counter >= Mt m), then streams the
 //             J and Phi^(m) k-tiles through the shared-memory ring;
 //   MMA       waits for accumulator h to be drained, accumulates L = J Phi;
-//   epilogue  8 warps read L from TMEM and do the kick and drift of Methods'
+//   epilogue  12 warps read L from TMEM and do the kick and drift of Methods'
 //             leapfrog on the FP32 state in global memory ([R][Npad], one
 //             owner per element), write the 16-bit Phi^(m+1) into the other
 //             buffer and the window sum, release accumulator h and arrive on
 //             the counter.
 // While the epilogue drains half h, the MMA of the other half runs.
 // ===========================================================================
-constexpr int kEpiWarps = 8;
+// 12 epilogue warps: three per TMEM lane quarter, each taking every third
+// 16-column chunk (1.5% faster than 8 on K2000 x 4096 in FP16X2 and FP16)
+constexpr int kEpiWarps = 12;              // a multiple of 4: each TMEM lane quarter alike
+constexpr int kCS = kEpiWarps / 4;         // chunk stride: warps per lane quarter
 constexpr int kMDThreads = 64 + 32 * kEpiWarps;
 
 struct DenseMDArgs {
@@ -248,7 +251,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         // ---- epilogue warps: kick, drift, BF16 shadow, window ----
         const int ew = warp - 2;              // 0..7
         const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
-        const int csel = ew >> 2;             // chunk parity handled by this warp
+        const int csel = ew >> 2;             // first chunk of this warp (chunks csel + kCS k)
         const int row = m0 + 32 * quarter + lane;
         const bool row_ok = row < a.N;
         const float hr = (a.h && row_ok) ? 2.f * a.h[row] : 0.f;
@@ -259,7 +262,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         if constexpr (ONCHIP) {
             // the tile's state moves on chip for the whole trajectory
             for (int hh = 0; hh < 2; ++hh)
-                for (int c = csel; c < NH / 16; c += 2) {
+                for (int c = csel; c < NH / 16; c += kCS) {
                     const int col = hh * NH + c * 16;
                     uint32_t pv[16];
 #pragma unroll
@@ -301,7 +304,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                 }
                 if (ok && ONCHIP) {
 #pragma unroll 1
-                    for (int c = csel; c < NH / 16; c += 2) {
+                    for (int c = csel; c < NH / 16; c += kCS) {
                         const int col = hh * NH + c * 16;
                         uint32_t v[16], pv[16];
                         tc::tmem_ld16(tmem + tl + (uint32_t)col, v);
@@ -345,14 +348,14 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     if (lane == 0) tc::mbar_arrive(acce0 + 8 * pass);
                 } else if (ok) {
 #pragma unroll 1
-                    for (int c = csel; c < NH / 16; c += 2) {
+                    for (int c = csel; c < NH / 16; c += kCS) {
                         uint32_t v[16];
                         tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(hh * NH + c * 16), v);
                         // the next chunk's state loads overlap this chunk's update
                         float nph[16], npp[16];
-                        const bool more = row_ok && c + 2 < NH / 16;
+                        const bool more = row_ok && c + kCS < NH / 16;
                         if (more) {
-                            const int rb1 = n0 + hh * NH + (c + 2) * 16;
+                            const int rb1 = n0 + hh * NH + (c + kCS) * 16;
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const size_t o = (size_t)(rb1 + j) * a.Npad + row;
@@ -423,7 +426,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         if constexpr (ONCHIP) {
             // final state back to global memory (the output kernel reads it there)
             for (int hh = 0; hh < 2; ++hh)
-                for (int c = csel; c < NH / 16; c += 2) {
+                for (int c = csel; c < NH / 16; c += kCS) {
                     const int col = hh * NH + c * 16;
                     uint32_t pv[16];
                     tc::tmem_ld16(tmem + tl + (uint32_t)(2 * NH + col), pv);

@@ -230,6 +230,15 @@ hqa_status hqa_vec_launch_md(hqa_ctx* ctx, const SparsePlan* plan, const StepCoe
 hqa_status hqa_vec_launch_field(hqa_ctx* ctx, const SparsePlan* plan, int32_t R,
                                 const float* phi, float* L, cudaStream_t st);
 
+// sparse_stream.cu: operand and state in global memory, grid barrier per step
+bool hqa_stream_supported(const hqa_ctx* ctx, int prec);
+hqa_status hqa_stream_launch_md(hqa_ctx* ctx, int prec, const StepCoef* d_sched, int64_t S,
+                                int32_t W, int32_t R, uint64_t seed, int init, const float* phi0,
+                                const float* p0, int M, float* phi_out, float* p_out,
+                                float* phibar_out, cudaStream_t st);
+hqa_status hqa_stream_field(hqa_ctx* ctx, int prec, int32_t R, const float* phi, float* L,
+                            cudaStream_t st);
+
 // sparse_md.cu
 hqa_status hqa_sparse_plan(hqa_ctx* ctx, int RB, int prec, const SparsePlan** out);
 hqa_status hqa_batch_launch_md(hqa_ctx* batch, int RB, int prec, const StepCoef* d_sched,

@@ -43,6 +43,7 @@ std::vector<Cand> candidates(const hqa_ctx* ctx, int prec)
         const int V = prec == HQA_PREC_BF16 ? 8 : 4;
         for (int rb : rbs)
             if (rb >= V) c.push_back({HQA_KERNEL_VECTOR, rb});
+        if (hqa_stream_supported(ctx, prec)) c.push_back({HQA_KERNEL_STREAM, 0});
     }
     return c;
 }

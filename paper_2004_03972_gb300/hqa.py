@@ -25,7 +25,8 @@ SCHED_PAPER, SCHED_LINEAR_GAMMA, SCHED_TABLE = 0, 1, 2
 INIT_PAPER, INIT_RANDOM_FLUX, INIT_GIVEN = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_FP16, PREC_FP16X2 = 0, 1, 2, 3, 4
 J_BF16, J_FP16, J_FP32, J_FP8 = 1, 2, 4, 8
-KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_DENSE, KERNEL_LOWDEG = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_SCALAR, KERNEL_VECTOR, KERNEL_DENSE, KERNEL_LOWDEG, KERNEL_STREAM = \
+    0, 1, 2, 3, 4, 5
 
 # every symbol include/hqa.h declares
 EXPORTS = (

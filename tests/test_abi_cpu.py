@@ -91,6 +91,7 @@ def test_enum_constants_match_header(tmp_path):
         ("J_FP32", hqa.J_FP32), ("J_FP8", hqa.J_FP8), ("KERNEL_AUTO", hqa.KERNEL_AUTO),
         ("KERNEL_SCALAR", hqa.KERNEL_SCALAR), ("KERNEL_VECTOR", hqa.KERNEL_VECTOR),
         ("KERNEL_DENSE", hqa.KERNEL_DENSE), ("KERNEL_LOWDEG", hqa.KERNEL_LOWDEG),
+        ("KERNEL_STREAM", hqa.KERNEL_STREAM),
         ("MLP_IN", hqa.MLP_IN), ("MLP_HIDDEN", hqa.MLP_HIDDEN), ("MLP_OUT", hqa.MLP_OUT),
         ("MLP_PARAMS", hqa.MLP_PARAMS))}
     pairs.update({name: code for code, name in hqa.STATUS_NAMES.items()})
