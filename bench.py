@@ -258,6 +258,14 @@ def smem_peak(hqa, dev_index):
         return sm * 128 * 2070e6 / 1e9, "derived: SMs x 128 B/clk x 2070 MHz (probe unavailable)"
 
 
+def l2_peak(hqa):
+    """L2 read bandwidth (GB/s) from the library's microbenchmark, measured now."""
+    try:
+        return hqa.l2_bandwidth_probe(), "measured: hqa_probe_l2_bandwidth (16-byte ld.global.cg)"
+    except Exception:
+        return None, "unmeasured"
+
+
 def _src_sha(path):
     with open(path, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -308,6 +316,8 @@ def kernel_name(hqa, plan, prec_name):
         kseg = 2 if prec_name.endswith("X2") else 1
         f16 = "true" if prec_name.startswith("PREC_FP16") else "false"
         return f"k_dense_md<{plan['replicas_per_block'] // 2},*,{kseg},*,*,{f16}>"
+    if k == hqa.KERNEL_STREAM:
+        return f"k_sparse_stream<{'true' if prec_name == 'PREC_BF16' else 'false'}>"
     base = "k_sparse_md_vec" if k == hqa.KERNEL_VECTOR else "k_sparse_md"
     return f"{base}<{plan['replicas_per_block']},{'true' if prec_name == 'PREC_BF16' else 'false'}>"
 
@@ -751,10 +761,13 @@ def measure_surrogate(args, hqa, torch, timer, dev, ws, rank):
             t_md = timer(lambda k: ctx.run(S, R, seed=seed_base + k, sched=sched,
                                            precision=hqa.PREC_BF16, out=md_out), K, 1)
             tl = float(np.mean(t_md))
-            peak, src = smem_peak(hqa, dev.index if dev.index is not None else 0)
+            streaming = plan["kernel"] == hqa.KERNEL_STREAM
+            peak, src = l2_peak(hqa) if streaming else \
+                smem_peak(hqa, dev.index if dev.index is not None else 0)
             ach = inst.nnz * 2 * R * S / tl / 1e9
-            roof = {"bound": "smem", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "peak_source": src, "traffic": None,
+            roof = {"bound": "l2" if streaming else "smem", "achieved": ach, "peak": peak,
+                    "unit": "GB/s", "frac": ach / peak if peak else None, "peak_source": src,
+                    "traffic": None,
                     "kernel": kernel_name(hqa, plan, "PREC_BF16"), "launch_ms": 1e3 * tl,
                     "plan": plan, "workload": f"ER N={N} mean degree 8, {R} replicas, {S} steps"}
             pin = torch.empty((R, N), dtype=torch.float32).pin_memory()

@@ -549,6 +549,16 @@ hqa_status hqa_arm_wait_check(hqa_ctx* ctx, const uint32_t* flag, int64_t step, 
  * capture), CUDA, OOM. */
 hqa_status hqa_probe_smem_bandwidth(double* gbps, void* stream);
 
+/* L2 read bandwidth of the current device in GB/s (no counterpart in the
+ * paper: the measured peak for the roofline of the streaming sparse kernel,
+ * whose gathers are L2 reads).  Two CTAs of 1024 threads per SM read a buffer
+ * of half the L2 size with 16-byte ld.global.cg loads, 40 grid-stride passes
+ * per launch; the best of three timed launches (CUDA events on `stream`, after
+ * one warm-up) is returned in *gbps.  Synchronises `stream`; allocates and
+ * frees the buffer.  Errors: INVALID_ARG, UNSUPPORTED (during a capture),
+ * CUDA, OOM. */
+hqa_status hqa_probe_l2_bandwidth(double* gbps, void* stream);
+
 /* Waits for the context's work on `stream` and returns (and clears) the
  * latched device-side status. */
 hqa_status hqa_sync(hqa_ctx* ctx, void* stream);

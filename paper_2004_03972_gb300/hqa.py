@@ -38,7 +38,7 @@ EXPORTS = (
     "hqa_mlp_destroy", "hqa_run_features", "hqa_surrogate_readout",
     "hqa_capture_begin", "hqa_capture_end", "hqa_graph_launch", "hqa_graph_destroy",
     "hqa_autotune", "hqa_hmd", "hqa_energy_f64", "hqa_run_trace", "hqa_solve_sub_tabu",
-    "hqa_arm_wait_check", "hqa_probe_smem_bandwidth",
+    "hqa_arm_wait_check", "hqa_probe_smem_bandwidth", "hqa_probe_l2_bandwidth",
 )
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 6, 64, 2, 4738
 
@@ -144,6 +144,8 @@ def lib() -> C.CDLL:
             L.hqa_autotune.restype = C.c_int
             L.hqa_probe_smem_bandwidth.argtypes = [C.POINTER(C.c_double), vp]
             L.hqa_probe_smem_bandwidth.restype = C.c_int
+            L.hqa_probe_l2_bandwidth.argtypes = [C.POINTER(C.c_double), vp]
+            L.hqa_probe_l2_bandwidth.restype = C.c_int
             L.hqa_arm_wait_check.argtypes = [vp, vp, i64, i64]
             L.hqa_arm_wait_check.restype = C.c_int
             L.hqa_solve_sub_tabu.argtypes = [vp, i32, vp, vp, i32, i32, i32, vp, vp, vp]
@@ -207,6 +209,13 @@ def smem_bandwidth_probe(stream=None) -> float:
     v = C.c_double()
     _check(lib().hqa_probe_smem_bandwidth(C.byref(v), _stream_ptr(stream)),
            "hqa_probe_smem_bandwidth")
+    return v.value
+
+
+def l2_bandwidth_probe(stream=None) -> float:
+    """hqa_probe_l2_bandwidth: measured L2 read bandwidth of the current GPU, GB/s."""
+    v = C.c_double()
+    _check(lib().hqa_probe_l2_bandwidth(C.byref(v), _stream_ptr(stream)), "hqa_probe_l2_bandwidth")
     return v.value
 
 
