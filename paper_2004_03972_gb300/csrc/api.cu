@@ -101,7 +101,7 @@ void free_ctx_device(hqa_ctx* c)
                     c->d_h_i32,   c->d_sched, c->d_ws,     c->d_state,  c->d_sub,
                     c->d_status,  c->d_Jbf,   c->d_binst,  c->d_bwork, c->d_feat,
                     c->d_tune,    c->d_diag,   c->d_Jcat,  c->d_efx,   c->d_ld,
-                    c->d_ldwork,  c->d_Jh,     c->d_Jhcat, c->d_Jf32};
+                    c->d_ldwork,  c->d_Jh,     c->d_Jhcat, c->d_Jf32,  c->d_ebits};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }

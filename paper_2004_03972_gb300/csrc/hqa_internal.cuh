@@ -196,6 +196,8 @@ struct hqa_ctx {
     // plain FP32 dense path (CUDA cores): J in FP32, [Npad32][Npad32], built on first use
     float* d_Jf32 = nullptr;
     int Npad32 = 0;
+    // bit-mask integer energy (readout.cu): word-major nonzero and negative masks, degrees
+    void* d_ebits = nullptr;
 };
 
 // Ensures *p holds at least `bytes` device bytes (frees and reallocates;
@@ -294,6 +296,10 @@ hqa_status hqa_launch_readout(hqa_ctx* ctx, int32_t R, const float* phibar, int3
                               int8_t* spins, uint8_t* frozen, int32_t* tally, cudaStream_t st);
 hqa_status hqa_launch_energy(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,
                              int64_t* cut, cudaStream_t st);
+// may_allocate = false: never allocates (the bit-mask tables are used only when
+// an earlier call built them; otherwise the per-coupling kernel runs)
+hqa_status hqa_launch_energy_ex(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,
+                                int64_t* cut, cudaStream_t st, bool may_allocate);
 
 // subsolve.cu
 hqa_status hqa_launch_subsolve(hqa_ctx* ctx, int32_t R, const int8_t* spins,

@@ -9,6 +9,8 @@
 // Energy (Eq. (1)) and cut (Methods, "MAX-CUT and Ising spin-glass"):
 //   ordered = sum_i s_i sum_{j != i} J_ij s_j   (int32 per row, int64 total)
 //   H = ordered / 2 + sum_i h_i s_i,  C = (sum_{ij} J_ij - ordered) / 4.
+#include <vector>
+
 #include "hqa_internal.cuh"
 
 namespace {
@@ -140,6 +142,58 @@ __global__ void __launch_bounds__(kThreads) k_energy_csr(const int32_t* __restri
     const int r = blockIdx.x;
     energy_block(row_ptr, col, val, h, N, sumJ, spins + (size_t)r * N, energy ? energy + r : nullptr,
                  cut ? cut + r : nullptr);
+}
+
+// Integer energy for couplings in {-1, 0, +1} with many couplings per row
+// (dense instances), from bit masks instead of per-coupling gathers.  With
+// bit j of a spin mask set where s_j = -1, and per row i the masks of its
+// nonzero couplings (nz) and of its negative ones (neg), a term J_ij s_j is
+// -1 exactly where (neg_i XOR S) AND nz_i has a bit, so
+//   g_i = sum_j J_ij s_j = deg_i - 2 popc((neg_i ^ S) & nz_i),
+// and sum_i s_i g_i is summed in int64 as in energy_block.  The row masks are
+// stored word-major ([word][row]), so the 32 lanes of a warp, one row each,
+// read one coalesced 128-byte line per word; a warp owns one replica and
+// builds its spin mask in shared memory by ballots.
+constexpr int kBitsWarps = 8;
+
+__global__ void __launch_bounds__(kBitsWarps * 32)
+k_energy_bits(const uint32_t* __restrict__ nzT, const uint32_t* __restrict__ negT,
+              const int32_t* __restrict__ deg, const int32_t* __restrict__ h, int N, int Wd,
+              int Npad, int R, int64_t sumJ, const int8_t* __restrict__ spins, int64_t* energy,
+              int64_t* cut)
+{
+    extern __shared__ uint32_t smask[];   // [kBitsWarps][Wd]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * kBitsWarps + warp;
+    if (r >= R) return;                   // whole warp: no block-wide barrier below
+    uint32_t* S = smask + (size_t)warp * Wd;
+    const int8_t* s = spins + (size_t)r * N;
+    for (int w = 0; w < Wd; ++w) {
+        const int j = 32 * w + lane;
+        const uint32_t b = __ballot_sync(0xffffffffu, j < N && s[j] < 0);
+        if (lane == 0) S[w] = b;
+    }
+    __syncwarp();
+    long long ordered = 0, field = 0;
+    for (int i0 = 0; i0 < N; i0 += 32) {
+        const int i = i0 + lane;
+        int cnt = 0;
+        for (int w = 0; w < Wd; ++w)
+            cnt += __popc((negT[(size_t)w * Npad + i] ^ S[w]) & nzT[(size_t)w * Npad + i]);
+        if (i < N) {
+            const int si = ((S[i >> 5] >> (i & 31)) & 1u) ? -1 : 1;
+            ordered += (long long)si * (long long)(deg[i] - 2 * cnt);
+            if (h) field += (long long)h[i] * si;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ordered += __shfl_xor_sync(0xffffffffu, ordered, o);
+        field += __shfl_xor_sync(0xffffffffu, field, o);
+    }
+    if (lane == 0) {
+        if (energy) energy[r] = ordered / 2 + field;
+        if (cut) cut[r] = (sumJ - ordered) / 4;
+    }
 }
 
 // Ising energy for real-valued couplings and fields (Results Eq. (1)), exact up
@@ -345,11 +399,72 @@ extern "C" hqa_status hqa_energy_f64(hqa_ctx* ctx, int32_t replicas, const int8_
     return hqa_capture_note(cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA);
 }
 
+// Word-major row masks of the couplings (k_energy_bits), built on first use.
+static hqa_status energy_bits_setup(hqa_ctx* ctx)
+{
+    if (ctx->d_ebits) return HQA_OK;
+    if (hqa_capturing()) return hqa_capture_note(HQA_ERR_UNSUPPORTED);
+    const int N = ctx->N, Wd = (N + 31) / 32, Npad = Wd * 32;
+    std::vector<uint32_t> nz((size_t)Wd * Npad, 0u), neg((size_t)Wd * Npad, 0u);
+    std::vector<int32_t> deg(N, 0);
+    for (int i = 0; i < N; ++i)
+        for (int64_t k = ctx->row_ptr[i]; k < ctx->row_ptr[i + 1]; ++k) {
+            const int j = ctx->col[k];
+            nz[(size_t)(j >> 5) * Npad + i] |= 1u << (j & 31);
+            if (ctx->val[k] < 0.f) neg[(size_t)(j >> 5) * Npad + i] |= 1u << (j & 31);
+            ++deg[i];
+        }
+    const size_t mb = nz.size() * sizeof(uint32_t);
+    void* d = nullptr;
+    HQA_CUDA_TRY(cudaMalloc(&d, 2 * mb + (size_t)N * sizeof(int32_t)));
+    char* b = static_cast<char*>(d);
+    if (cudaMemcpy(b, nz.data(), mb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b + mb, neg.data(), mb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b + 2 * mb, deg.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaFree(d);
+        (void)cudaGetLastError();
+        return HQA_ERR_CUDA;
+    }
+    ctx->d_ebits = d;
+    ++ctx->generation;
+    return HQA_OK;
+}
+
+// The bit-mask energy pays where rows hold at least as many couplings as mask
+// words (dense instances); sparse rows keep the per-coupling gather.
+static bool energy_bits_wanted(const hqa_ctx* ctx)
+{
+    const int Wd = (ctx->N + 31) / 32;
+    return ctx->unit && ctx->nnz >= (int64_t)ctx->N * Wd;
+}
+
 hqa_status hqa_launch_energy(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,
                              int64_t* cut, cudaStream_t st)
 {
+    return hqa_launch_energy_ex(ctx, R, spins, energy, cut, st, true);
+}
+
+hqa_status hqa_launch_energy_ex(hqa_ctx* ctx, int32_t R, const int8_t* spins, int64_t* energy,
+                                int64_t* cut, cudaStream_t st, bool may_allocate)
+{
     if (!ctx->integer) return HQA_ERR_UNSUPPORTED;
     if (R <= 0) return HQA_OK;
+    // without permission to allocate, the bit masks are used only if already built
+    if (energy_bits_wanted(ctx) && (may_allocate || ctx->d_ebits)) {
+        hqa_status s = energy_bits_setup(ctx);
+        if (s != HQA_OK) return s;
+        const int N = ctx->N, Wd = (N + 31) / 32, Npad = Wd * 32;
+        const size_t mb = (size_t)Wd * Npad * sizeof(uint32_t);
+        const char* b = static_cast<const char*>(ctx->d_ebits);
+        const size_t smem = (size_t)kBitsWarps * Wd * sizeof(uint32_t);
+        if (smem > 48 * 1024) return HQA_ERR_TOO_LARGE;   // N <= 49152
+        k_energy_bits<<<(R + kBitsWarps - 1) / kBitsWarps, kBitsWarps * 32, smem, st>>>(
+            reinterpret_cast<const uint32_t*>(b), reinterpret_cast<const uint32_t*>(b + mb),
+            reinterpret_cast<const int32_t*>(b + 2 * mb), ctx->has_h ? ctx->d_h_i32 : nullptr, N,
+            Wd, Npad, R, ctx->sum_J_all, spins, energy, cut);
+        return cudaGetLastError() == cudaSuccess ? HQA_OK : HQA_ERR_CUDA;
+    }
     k_energy_csr<<<R, kThreads, 0, st>>>(ctx->d_row_ptr, ctx->d_col, ctx->d_val_i8,
                                          ctx->has_h ? ctx->d_h_i32 : nullptr, ctx->N,
                                          ctx->sum_J_all, spins, energy, cut);

@@ -617,7 +617,7 @@ static hqa_status solve_sub_noalloc_impl(hqa_ctx* ctx, int32_t replicas, const i
     k_sub_enum<<<grid, kEnumThreads, 0, st>>>(prep, LB, keys);
     k_sub_assemble<<<R, 256, 0, st>>>(prep, keys, ctx->N, spins, out_spins);
     if (cudaGetLastError() != cudaSuccess) return HQA_ERR_CUDA;
-    if (out_energy) return hqa_launch_energy(ctx, R, out_spins, out_energy, nullptr, st);
+    if (out_energy) return hqa_launch_energy_ex(ctx, R, out_spins, out_energy, nullptr, st, false);
     return HQA_OK;
 }
 
