@@ -716,7 +716,8 @@ def measure_surrogate(args, hqa, torch, timer, dev, ws, rank):
                 res = []
                 Kg = min(K, 2)
                 t = timer(lambda k, gc=gc: res.append(SG.gated_run(ctx, mlp, gc, R,
-                                                                   seed=seed_base + 1000 + k)),
+                                                                   seed=seed_base + 1000 + k,
+                                                                   score_all=False)),
                           Kg, 1)
                 res = res[-Kg:]
                 cuts = np.concatenate([g["cut"].cpu().numpy() for g in res])

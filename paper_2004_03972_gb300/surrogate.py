@@ -6,10 +6,10 @@ module sequences the calls.
                 and labels from the full run of the same trajectory:
                 label 0 = spin ends frozen (rank split with n), label 1 = s = +1
   train()       minibatch AdamW on hqa_mlp_grad
-  gated_run()   features -> network -> surrogate readout -> exact sub-solve for every
-                replica; replicas the gate does not accept resume the MD from the
-                feature point to the full length (the fallback) and take the
-                method's own readout + sub-solve
+  gated_run()   features -> network -> surrogate readout -> exact sub-solve of the
+                accepted replicas (of every replica when scoring); replicas the gate
+                does not accept resume the MD from the feature point to the full
+                length (the fallback) and take the method's own readout + sub-solve
 """
 from __future__ import annotations
 
@@ -68,9 +68,11 @@ def train(mlp, xs, ys, epochs=30, batch=16384, lr=2e-3, weight_decay=1e-4, seed=
     return hist
 
 
-def gated_run(ctx, mlp, cfg: SurrogateConfig, replicas, seed, sched=None):
+def gated_run(ctx, mlp, cfg: SurrogateConfig, replicas, seed, sched=None, score_all=True):
     """Returns dict with spins/energy/cut per replica (device), accept mask, the
-    surrogate-only results for every replica, and the MD steps actually spent."""
+    surrogate-only results (score_all: for every replica, which costs a sub-solve of
+    the rejected replicas too; else only for the accepted ones, the gated form's
+    own work), and the MD steps actually spent."""
     import torch
     sched = sched or hqa.schedule()
     sched.n_ambivalent = cfg.n_ambivalent
@@ -80,16 +82,25 @@ def gated_run(ctx, mlp, cfg: SurrogateConfig, replicas, seed, sched=None):
                                  segments=cfg.segments, precision=cfg.precision)
     logits = mlp.forward(x, precision=cfg.precision)
     s_sur, f_sur, accept, err = ctx.surrogate_readout(logits, R, n, cfg.max_expected_errors)
-    sub_s, sub_e = ctx.solve_sub(s_sur, f_sur, n)
-    e_sur, c_sur = ctx.energy(sub_s)
-    # fallback: the replicas the gate rejected resume the MD from the feature point to the
-    # full length (bitwise the full trajectory) and take the method's own readout
     acc = accept.bool()
     rej = (~acc).nonzero().squeeze(1)
     n_fallback = int(rej.numel())
-    out = {"accept": acc, "expected_errors": err, "surrogate_spins": sub_s,
-           "surrogate_energy": e_sur, "surrogate_cut": c_sur}
-    spins = sub_s.clone()
+    out = {"accept": acc, "expected_errors": err}
+    if score_all:
+        sub_s, sub_e = ctx.solve_sub(s_sur, f_sur, n)
+        e_sur, c_sur = ctx.energy(sub_s)
+        out.update(surrogate_spins=sub_s, surrogate_energy=e_sur, surrogate_cut=c_sur)
+        spins = sub_s.clone()
+    else:
+        # the exact sub-solve only where the gate stopped the replica
+        spins = s_sur.clone()
+        aidx = acc.nonzero().squeeze(1)
+        if int(aidx.numel()):
+            a_s, _ = ctx.solve_sub(s_sur.index_select(0, aidx).contiguous(),
+                                   f_sur.index_select(0, aidx).contiguous(), n)
+            spins[aidx] = a_s
+    # fallback: the replicas the gate rejected resume the MD from the feature point to the
+    # full length (bitwise the full trajectory) and take the method's own readout
     if n_fallback:
         rest = ctx.run(cfg.steps - cfg.steps_c, n_fallback, sched=sched, dt=dt,
                        precision=cfg.precision, init=hqa.INIT_GIVEN,

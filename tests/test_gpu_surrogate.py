@@ -170,5 +170,8 @@ def test_gate_accepts_and_is_scored(hqa):
     assert torch.equal(g["spins"][rej], full["spins"][rej])
     assert torch.equal(g["cut"][rej], full["cut"][rej])
     assert torch.equal(g["cut"][~rej], g["surrogate_cut"][~rej])
+    # the timed form sub-solves only the accepted replicas: the same results
+    lean = SG.gated_run(test, mlp, cfg, R, seed=3, score_all=False)
+    assert torch.equal(lean["spins"], g["spins"]) and torch.equal(lean["cut"], g["cut"])
     print(f"\n60%, threshold {cfg.max_expected_errors:.0f}: accepted {acc.sum()} of {R}, "
           f"mislabel {np.median(mis[acc]):.3f}, median cut loss {np.median(loss[acc]):.0f}")
