@@ -214,3 +214,33 @@ def test_batch_spilled_state_bitwise(hqa):
                           kernel=hqa.KERNEL_SCALAR, outputs=(key,))
             c.sync()
             assert torch.equal(views[k], alone[key]), (k, key)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 1e-2)])
+def test_full_uneven512_batch_states(hqa, orc, prec, tol):
+    """The benchmark's whole 512-member batch at its replica count (64) in the launch
+    shape the autotuner picks for it (the low-degree kernel, 2 replicas per block):
+    states after 100 steps of sampled members and replicas against the oracle, and
+    the readout, int64 energies and cuts of sampled replicas exact."""
+    insts = instances.uneven_batch(512, 200, 5000, 1400)
+    ctxs = [hqa.Context.from_instance(i) for i in insts]
+    batch = hqa.Context.batch(ctxs)
+    R, S, seed, dt, n = 64, 100, 9, 1e-4, 24
+    out = batch.run(S, R, seed=seed, dt=dt, precision=prec, replicas_per_block=2,
+                    kernel=hqa.KERNEL_LOWDEG, sched=hqa.schedule(n_ambivalent=n))
+    batch.sync()
+    phis, ps, pbar = (batch.split(out[k], R) for k in ("phi", "p", "phibar"))
+    spins = batch.split(out["spins"], R)
+    for k in (0, 1, 255, 511):
+        pr = orc.Problem.from_instance(insts[k])
+        for r in (0, 37, R - 1):
+            p0 = orc.initial_momenta(member_seed(seed, k), r, insts[k].N)
+            ophi, op, _ = orc.md_run(pr, S, dt=dt, p0=p0, window=100)
+            g_phi = phis[k][r].cpu().numpy().astype(np.float64)
+            g_p = ps[k][r].cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(g_phi - ophi)) <= tol * np.max(np.abs(ophi))
+            assert np.max(np.abs(g_p - op)) <= tol * max(1.0, np.max(np.abs(op)))
+            s, _ = orc.readout(pbar[k][r].cpu().numpy().astype(np.float64), n)
+            assert np.array_equal(spins[k][r].cpu().numpy(), s)
+            assert int(out["energy"][k * R + r]) == orc.energy_int(pr, s)
+            assert int(out["cut"][k * R + r]) == orc.cut_int(pr, s)
