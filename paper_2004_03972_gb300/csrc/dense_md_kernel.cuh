@@ -249,7 +249,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         }
     } else {
         // ---- epilogue warps: kick, drift, BF16 shadow, window ----
-        const int ew = warp - 2;              // 0..7
+        const int ew = warp - 2;              // 0 .. kEpiWarps - 1
         const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
         const int csel = ew >> 2;             // first chunk of this warp (chunks csel + kCS k)
         const int row = m0 + 32 * quarter + lane;
