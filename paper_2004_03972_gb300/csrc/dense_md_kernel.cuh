@@ -90,18 +90,21 @@ static __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
     return v;
 }
 
-template <int NH, int STAGES, int KSEG, bool FUSED, bool ONCHIP, bool F16>
+template <int NH, int STAGES, int KSEG, bool FUSED, bool ONCHIP, bool F16, int KSUB, bool PHIT>
 __global__ void __launch_bounds__(kMDThreads, 1)
 k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
            const DenseMDArgs a)
 {
+    // a ring stage holds KSUB consecutive 64-wide k-tiles: the KSUB J tiles,
+    // then the KSUB phi tiles, then (FUSED, SHAREJ) the KSUB second phi tiles
     constexpr uint32_t A_BYTES = BM * BK * 2;
     constexpr uint32_t B_BYTES = NH * BK * 2;
     // fused: one J tile per stage feeds the MMAs of both column halves.
     // SHAREJ (split phi against an exact J): one J tile per stage feeds the
     // MMAs of both K segments, phi_hi and phi_lo, into the same accumulator
     constexpr bool SHAREJ = KSEG == 2 && !FUSED;
-    constexpr uint32_t STAGE_BYTES = A_BYTES + ((FUSED || SHAREJ) ? 2u : 1u) * B_BYTES;
+    constexpr uint32_t STAGE_BYTES = KSUB * (A_BYTES + ((FUSED || SHAREJ) ? 2u : 1u) * B_BYTES);
+    constexpr uint32_t B2_OFF = KSUB * (A_BYTES + B_BYTES);   // second phi tiles
     constexpr int NPASS = FUSED ? 1 : 2;   // MMA passes (and counters) per step
     // on-chip state: p in TMEM columns [2 NH, 4 NH), phi in shared memory
     constexpr uint32_t TMEM_COLS = ONCHIP ? 512u
@@ -109,13 +112,19 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
     static_assert(NH % 16 == 0 && NH <= 256, "UMMA N");
     static_assert(!ONCHIP || (NH <= 128 && !FUSED), "on-chip state: 4 NH TMEM columns");
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+    static_assert((KSUB == 1 || KSUB == 2) && (KSUB == 1 || !FUSED), "k-tiles per stage");
+    static_assert(!PHIT || ONCHIP, "phi in TMEM is an on-chip state form");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t bar = base + STAGES * STAGE_BYTES;
     const uint32_t full0 = bar, empty0 = bar + 8 * STAGES;
     const uint32_t accf0 = bar + 16 * STAGES, acce0 = accf0 + 16;
     const uint32_t tmem_slot = acce0 + 16;
-    const uint32_t phis = bar + 1024;   // ONCHIP: phi tile [2 NH columns][128 rows] FP32
+    // ONCHIP: TMEM columns [2 NH, 4 NH) hold one state word of the tile's 2 NH
+    // replicas: p, with phi in a shared-memory tile [2 NH columns][128 rows]
+    // FP32 at phis; or (PHIT) phi, with p in global memory and the whole
+    // shared memory left to the ring
+    const uint32_t phis = bar + 1024;
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.Mt, nc = blockIdx.x / a.Mt;
@@ -183,22 +192,27 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     // [J_hi | J_lo | J_hi] (KSEG 3); with KSEG 2 a stage holds the
                     // J tile and the hi and lo tiles of the same k (columns kt and
                     // Npad + kt of the [hi | lo] operand rows)
-                    const int KTT = SHAREJ ? a.KT : KSEG * a.KT;
-                    for (int kt = 0; kt < KTT; ++kt, ++it) {
+                    const int KTT = SHAREJ ? a.KT : KSEG * a.KT;   // a multiple of KSUB
+                    for (int kt = 0; kt < KTT; kt += KSUB, ++it) {
                         const int s = it % STAGES;
                         if (it >= STAGES &&
                             !tc::mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort, kWaitNs))
                             break;
                         const uint32_t sa = base + s * STAGE_BYTES;
                         tc::mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-                        tc::tma_load_2d(sa, &tmJ, kt * BK, m0, full0 + 8 * s);
-                        tc::tma_load_2d(sa + A_BYTES, &tmB, kt * BK, brow, full0 + 8 * s);
-                        if constexpr (FUSED)
-                            tc::tma_load_2d(sa + A_BYTES + B_BYTES, &tmB, kt * BK, brow + NH,
+#pragma unroll
+                        for (int u = 0; u < KSUB; ++u) {
+                            const int k = (kt + u) * BK;
+                            tc::tma_load_2d(sa + u * A_BYTES, &tmJ, k, m0, full0 + 8 * s);
+                            tc::tma_load_2d(sa + KSUB * A_BYTES + u * B_BYTES, &tmB, k, brow,
                                             full0 + 8 * s);
-                        if constexpr (SHAREJ)
-                            tc::tma_load_2d(sa + A_BYTES + B_BYTES, &tmB, a.Npad + kt * BK, brow,
-                                            full0 + 8 * s);
+                            if constexpr (FUSED)
+                                tc::tma_load_2d(sa + B2_OFF + u * B_BYTES, &tmB, k, brow + NH,
+                                                full0 + 8 * s);
+                            if constexpr (SHAREJ)
+                                tc::tma_load_2d(sa + B2_OFF + u * B_BYTES, &tmB, a.Npad + k, brow,
+                                                full0 + 8 * s);
+                        }
                     }
                 }
             }
@@ -219,27 +233,32 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     tc::tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(hh * NH);
                     const int KTT = SHAREJ ? a.KT : KSEG * a.KT;
-                    for (int kt = 0; kt < KTT; ++kt, ++it) {
+                    for (int kt = 0; kt < KTT; kt += KSUB, ++it) {
                         const int s = it % STAGES;
                         if (!tc::mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort, kWaitNs)) break;
                         tc::tc_fence_after();
                         const uint32_t sa = base + s * STAGE_BYTES;
-                        const uint64_t ad = tc::sdesc_k128(sa), bd = tc::sdesc_k128(sa + A_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk)
-                            tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
-                        if constexpr (FUSED) {
-                            const uint64_t bd1 = tc::sdesc_k128(sa + A_BYTES + B_BYTES);
-#pragma unroll
-                            for (int kk = 0; kk < BK / 16; ++kk)
-                                tc::mma_bf16(d + (uint32_t)NH, ad + 2 * kk, bd1 + 2 * kk, idesc,
-                                             (kt | kk) != 0);
-                        }
-                        if constexpr (SHAREJ) {   // J phi_lo into the same accumulator
-                            const uint64_t bd1 = tc::sdesc_k128(sa + A_BYTES + B_BYTES);
+                        for (int u = 0; u < KSUB; ++u) {
+                            const uint64_t ad = tc::sdesc_k128(sa + u * A_BYTES);
+                            const uint64_t bd = tc::sdesc_k128(sa + KSUB * A_BYTES + u * B_BYTES);
+                            const bool first = (kt | u) == 0;
 #pragma unroll
                             for (int kk = 0; kk < BK / 16; ++kk)
-                                tc::mma_bf16(d, ad + 2 * kk, bd1 + 2 * kk, idesc, 1u);
+                                tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, !(first && kk == 0));
+                            if constexpr (FUSED) {
+                                const uint64_t bd1 = tc::sdesc_k128(sa + B2_OFF + u * B_BYTES);
+#pragma unroll
+                                for (int kk = 0; kk < BK / 16; ++kk)
+                                    tc::mma_bf16(d + (uint32_t)NH, ad + 2 * kk, bd1 + 2 * kk, idesc,
+                                                 !(first && kk == 0));
+                            }
+                            if constexpr (SHAREJ) {   // J phi_lo into the same accumulator
+                                const uint64_t bd1 = tc::sdesc_k128(sa + B2_OFF + u * B_BYTES);
+#pragma unroll
+                                for (int kk = 0; kk < BK / 16; ++kk)
+                                    tc::mma_bf16(d, ad + 2 * kk, bd1 + 2 * kk, idesc, 1u);
+                            }
                         }
                         tc::mma_commit(empty0 + 8 * s);
                     }
@@ -268,9 +287,13 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const size_t o = (size_t)(n0 + col + j) * a.Npad + row;
-                        asm volatile("st.shared.f32 [%0], %1;" ::"r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u),
-                                     "f"(a.phi[o]));
-                        pv[j] = __float_as_uint(a.p[o]);
+                        if constexpr (PHIT) {
+                            pv[j] = __float_as_uint(a.phi[o]);
+                        } else {
+                            asm volatile("st.shared.f32 [%0], %1;"
+                                         ::"r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u), "f"(a.phi[o]));
+                            pv[j] = __float_as_uint(a.p[o]);
+                        }
                     }
                     tc::tmem_st16(tmem + tl + (uint32_t)(2 * NH + col), pv);
                 }
@@ -287,12 +310,12 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                 // the state of this warp's first chunk does not depend on the MMA:
                 // its loads are in flight while the accumulator is computed
                 float ph[16], pp[16];
-                if (!ONCHIP && row_ok && csel < NH / 16) {
+                if ((!ONCHIP || PHIT) && row_ok && csel < NH / 16) {
                     const int rb0 = n0 + hh * NH + csel * 16;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const size_t o = (size_t)(rb0 + j) * a.Npad + row;
-                        ph[j] = a.phi[o];
+                        if constexpr (!ONCHIP) ph[j] = a.phi[o];
                         pp[j] = a.p[o];
                     }
                 }
@@ -302,7 +325,60 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                     tc::mbar_wait(accf0 + 8 * pass, (uint32_t)(m & 1), abort, kWaitNs));
                     tc::tc_fence_after();
                 }
-                if (ok && ONCHIP) {
+                if (ok && PHIT) {
+                    // phi in TMEM next to the accumulators, p in global memory
+#pragma unroll 1
+                    for (int c = csel; c < NH / 16; c += kCS) {
+                        const int col = hh * NH + c * 16;
+                        uint32_t v[16], fv[16];
+                        tc::tmem_ld16(tmem + tl + (uint32_t)col, v);
+                        tc::tmem_ld16(tmem + tl + (uint32_t)(2 * NH + col), fv);
+                        // the next chunk's momenta load while this chunk updates
+                        float npp[16];
+                        const bool more = row_ok && c + kCS < NH / 16;
+                        if (more) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                npp[j] = a.p[(size_t)(n0 + col + 16 * kCS + j) * a.Npad + row];
+                        }
+                        tc::tmem_wait_ld();
+                        if (row_ok) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const size_t o = (size_t)(n0 + col + j) * a.Npad + row;
+                                const float f = __uint_as_float(fv[j]);
+                                const float L = __uint_as_float(v[j]) * a.lscale + hr * fabsf(f);
+                                const float phi2 = f * f;
+                                float pw = f;
+                                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                                const float pn = pp[j] - fmaf(cf.x, pw, cf.y * L);
+                                const float fn = fmaf(cf.z, pn, f);
+                                a.p[o] = pn;
+                                fv[j] = __float_as_uint(fn);
+                                const size_t ob = (size_t)(n0 + col + j) * Kb + row;
+                                const float fs = fn * a.oscale;
+                                const uint16_t hi = cvt16<F16>(fs);
+                                nb[ob] = hi;
+                                if (KSEG == 2) nb[ob + a.Npad] = cvt16<F16>(fs - from16<F16>(hi));
+                                if (KSEG == 3) {
+                                    nb[ob + a.Npad] = hi;
+                                    nb[ob + 2 * a.Npad] = cvt16<F16>(fs - from16<F16>(hi));
+                                }
+                                if (in_win) a.w[o] += fn;
+                            }
+                        }
+                        // .sync.aligned: every lane of the warp, outside the row_ok branch
+                        tc::tmem_st16(tmem + tl + (uint32_t)(2 * NH + col), fv);
+                        tc::tmem_wait_st();
+                        if (more) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) pp[j] = npp[j];
+                        }
+                    }
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(acce0 + 8 * pass);
+                } else if (ok && ONCHIP) {
 #pragma unroll 1
                     for (int c = csel; c < NH / 16; c += kCS) {
                         const int col = hh * NH + c * 16;
@@ -434,11 +510,15 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const size_t o = (size_t)(n0 + col + j) * a.Npad + row;
-                        float f;
-                        asm volatile("ld.shared.f32 %0, [%1];"
-                                     : "=f"(f) : "r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u));
-                        a.phi[o] = f;
-                        a.p[o] = __uint_as_float(pv[j]);
+                        if constexpr (PHIT) {   // p is already in global memory
+                            a.phi[o] = __uint_as_float(pv[j]);
+                        } else {
+                            float f;
+                            asm volatile("ld.shared.f32 %0, [%1];"
+                                         : "=f"(f) : "r"(phis + (uint32_t)(col + j) * 512u + rloc * 4u));
+                            a.phi[o] = f;
+                            a.p[o] = __uint_as_float(pv[j]);
+                        }
                     }
                 }
         }
@@ -524,13 +604,13 @@ static __global__ void k_dense_out(DenseMDArgs a, float inv_w, float* phi_out, f
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_NONFINITE);
 }
 
-template <int NH, int STAGES, bool TWOB, bool ONCHIP>
+template <int NH, int STAGES, bool TWOB, bool ONCHIP, int KSUB, bool PHIT>
 size_t md_smem()
 {
-    // alignment slack, ring (one J tile and one or two phi tiles per stage),
-    // barrier block (1 KB), on-chip phi tile
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + (TWOB ? 2 : 1) * NH * BK * 2) + 1024 +
-           (ONCHIP ? (size_t)2 * NH * BM * 4 : 0);
+    // alignment slack, ring (KSUB J tiles and KSUB or 2 KSUB phi tiles per
+    // stage), barrier block (1 KB), shared-memory phi tile (on chip, not PHIT)
+    return 1024 + (size_t)STAGES * KSUB * (BM * BK * 2 + (TWOB ? 2 : 1) * NH * BK * 2) + 1024 +
+           (ONCHIP && !PHIT ? (size_t)2 * NH * BM * 4 : 0);
 }
 
 // The tile's state (phi, p) stays on chip for the whole trajectory when its
@@ -550,11 +630,28 @@ constexpr bool kFusedHalves = false;
 // Deeper rings measured no faster on K2000 x 4096: with the state in global
 // memory instead (freeing the 128 KB phi tile), 4 and 7 stages ran FP16X2 in
 // 115.5 ms per 2000 steps against 114.2 on chip, FP16 in 84.3 and 87.6 against 77.8.
-constexpr int md_stages(int nh, bool twob, bool onchip)
+constexpr int md_stages(int nh, bool twob, bool onchip, int ksub, bool phit)
 {
-    const int stage = BM * BK * 2 + (twob ? 2 : 1) * nh * BK * 2;
-    const int n = (227 * 1024 - 2048 - 64 - (onchip ? 2 * nh * BM * 4 : 0)) / stage;
-    return n > 4 ? 4 : n;
+    const int stage = ksub * (BM * BK * 2 + (twob ? 2 : 1) * nh * BK * 2);
+    const int n = (227 * 1024 - 2048 - 64 - (onchip && !phit ? 2 * nh * BM * 4 : 0)) / stage;
+    const int cap = phit ? 8 : 4;
+    return n > cap ? cap : n;
+}
+
+// On-chip state form for NH <= 128: phi in TMEM next to the accumulators and
+// p in global memory (L2-resident), so that the ring gets the 128 KB a
+// shared-memory phi tile would take; and two 64-wide k-tiles per ring stage.
+// The MMA-issuing thread pays a fixed cost per stage (observing the full
+// barrier, the commit) that a 64-wide stage of N = 128 MMAs does not hide;
+// on K2000 x 4096, 2000 steps: FP16X2 114.7 -> 108.3 ms (phi in TMEM, 4
+// stages of one k-tile) -> 105.8 ms (2 stages of two), FP16 78.0 -> 84.0 ->
+// 69.3 ms, all bitwise identical.
+constexpr bool kPhiInTmem = true;
+constexpr int kKSub = 2;
+
+constexpr int md_ksub(int nh, bool twob, bool onchip, bool phit)
+{
+    return kKSub > 1 && phit && md_stages(nh, twob, onchip, 2, phit) >= 2 ? 2 : 1;
 }
 
 // Column halves: NH replicas (multiple of 16, <= 256); Nc = ceil(R / 2NH) with
@@ -583,11 +680,14 @@ hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaS
 {
     constexpr bool ONCHIP = onchip_ok(NH) && !kFusedHalves;
     constexpr bool TWOB = kFusedHalves || KSEG == 2;   // two phi tiles per ring stage
-    constexpr int STAGES = md_stages(NH, TWOB, ONCHIP);
+    constexpr bool PHIT = ONCHIP && kPhiInTmem;
+    constexpr int KSUB = kFusedHalves ? 1 : md_ksub(NH, TWOB, ONCHIP, PHIT);
+    constexpr int STAGES = md_stages(NH, TWOB, ONCHIP, KSUB, PHIT);
     static_assert(STAGES >= 2, "ring depth");
-    const size_t smem = md_smem<NH, STAGES, TWOB, ONCHIP>();
+    const size_t smem = md_smem<NH, STAGES, TWOB, ONCHIP, KSUB, PHIT>();
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
-    const void* fn = (const void*)k_dense_md<NH, STAGES, KSEG, kFusedHalves, ONCHIP, F16>;
+    if (a.KT % KSUB != 0) return HQA_ERR_INVALID_ARG;   // Npad is a multiple of 128
+    const void* fn = (const void*)k_dense_md<NH, STAGES, KSEG, kFusedHalves, ONCHIP, F16, KSUB, PHIT>;
     if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
     void* args[] = {const_cast<CUtensorMap*>(&tmA), const_cast<CUtensorMap*>(&tmB),
                     const_cast<DenseMDArgs*>(&a)};
