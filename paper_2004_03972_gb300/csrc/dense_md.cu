@@ -184,19 +184,28 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 // 2-D 16-bit tensor [rows][cols] (BF16, or FP16 when f16; cols contiguous,
 // cols * 2 bytes a multiple of 16), box {64 cols, box_rows}, 128-byte swizzle.
-bool make_tmap16(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
-                 bool f16)
+// A [rows][cols] 16-bit array; box_cols x box_rows boxes, 128-byte swizzle
+// (MMA operand tiles) or none (row-major staging tiles).
+bool make_tmap16_box(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols,
+                     uint32_t box_cols, uint32_t box_rows, bool swizzle, bool f16)
 {
     auto enc = get_encode();
     if (!enc) return false;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
-                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+bool make_tmap16(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
+                 bool f16)
+{
+    return make_tmap16_box(m, ptr, rows, cols, BK, box_rows, true, f16);
 }
 
 template <int BN, int STAGES>
@@ -477,7 +486,13 @@ static hqa_status dense_md_chunk(hqa_ctx* ctx, const StepCoef* d_sched, int64_t 
         ctx->wait_flag = nullptr;
     }
     CUtensorMap tmB;
-    if (!make_tmap16(&tmB, a.phib, (uint64_t)2 * Rpad, (uint64_t)kseg * Npad, NH, f16))
+    // a CTA of a pair stages half of each NH-replica phi tile
+    const uint32_t box_rows = hqa_dense::use_pair(NH, Mt) ? NH / 2 : NH;
+    if (!make_tmap16(&tmB, a.phib, (uint64_t)2 * Rpad, (uint64_t)kseg * Npad, box_rows, f16))
+        return HQA_ERR_CUDA;
+    // the epilogue's operand stores: 128 spins x 16 replicas per box, unswizzled
+    CUtensorMap tmS;
+    if (!make_tmap16_box(&tmS, a.phib, (uint64_t)2 * Rpad, (uint64_t)kseg * Npad, 128, 16, false, f16))
         return HQA_ERR_CUDA;
     const CUtensorMap& tmA = f16 ? (kseg == 3 ? ctx->tmJh3 : ctx->tmJh)
                                  : (kseg == 3 ? ctx->tmJ3 : ctx->tmJ);
@@ -486,8 +501,8 @@ static hqa_status dense_md_chunk(hqa_ctx* ctx, const StepCoef* d_sched, int64_t 
     else hqa_dense::k_dense_init<false><<<g, 256, 0, st>>>(a, seed, init, phi0, p0, kseg);
     if (cudaMemsetAsync(a.gbar, 0, (size_t)2 * Nc * sizeof(unsigned int), st) != cudaSuccess)
         return HQA_ERR_CUDA;
-    s = f16 ? hqa_dense::dense_md_dispatch<true>(ctx, a, NH, kseg, grid, st, tmA, tmB)
-            : hqa_dense::dense_md_dispatch<false>(ctx, a, NH, kseg, grid, st, tmA, tmB);
+    s = f16 ? hqa_dense::dense_md_dispatch<true>(ctx, a, NH, kseg, grid, st, tmA, tmB, tmS)
+            : hqa_dense::dense_md_dispatch<false>(ctx, a, NH, kseg, grid, st, tmA, tmB, tmS);
     if (s != HQA_OK) return s;
     const int64_t nwin = S < W ? S : W;
     hqa_dense::k_dense_out<<<std::min<size_t>(8192, ((size_t)R * ctx->N + 255) / 256), 256, 0, st>>>(
@@ -524,7 +539,7 @@ hqa_status hqa_dense_launch_md(hqa_ctx* ctx, const StepCoef* d_sched, int64_t S,
 
 template hqa_status hqa_dense::dense_md_dispatch<false>(hqa_ctx*, const DenseMDArgs&, int, int, int,
                                                         cudaStream_t, const CUtensorMap&,
-                                                        const CUtensorMap&);
+                                                        const CUtensorMap&, const CUtensorMap&);
 
 extern "C" hqa_status hqa_arm_wait_check(hqa_ctx* ctx, const uint32_t* flag, int64_t step,
                                          int64_t limit_ns)

@@ -5,4 +5,5 @@
 
 template hqa_status hqa_dense::dense_md_dispatch<true>(hqa_ctx*, const hqa_dense::DenseMDArgs&,
                                                        int, int, int, cudaStream_t,
-                                                       const CUtensorMap&, const CUtensorMap&);
+                                                       const CUtensorMap&, const CUtensorMap&,
+                                                       const CUtensorMap&);

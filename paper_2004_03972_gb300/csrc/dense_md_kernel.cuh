@@ -55,12 +55,36 @@ __device__ __forceinline__ float from16(uint16_t u)
 //             buffer and the window sum, release accumulator h and arrive on
 //             the counter.
 // While the epilogue drains half h, the MMA of the other half runs.
+//
+// PAIR: the CTAs of row tiles 2t and 2t+1 of a column group form a 2-CTA
+// cluster and share one M = 256 MMA per K slice (cta_group::2), issued by the
+// even CTA.  Each CTA stages its own 128-row J tiles but only half of each
+// phi tile (NH/2 replicas); the MMA reads the other half from the peer's
+// shared memory, so an SM takes in a third (KSEG 2) or a quarter (KSEG 1)
+// fewer operand bytes from L2 per MMA cycle.  The odd CTA's MMA warp relays
+// each landed stage to the even CTA (remote mbarrier arrive); the MMA commits
+// arrive on both CTAs' barriers; the odd CTA's epilogue warps release the
+// accumulator on the even CTA's barrier.  Requires phi in TMEM.
 // ===========================================================================
 // 12 epilogue warps: three per TMEM lane quarter, each taking every third
 // 16-column chunk (1.5% faster than 8 on K2000 x 4096 in FP16X2 and FP16)
 constexpr int kEpiWarps = 12;              // a multiple of 4: each TMEM lane quarter alike
 constexpr int kCS = kEpiWarps / 4;         // chunk stride: warps per lane quarter
 constexpr int kMDThreads = 64 + 32 * kEpiWarps;
+
+// phi in TMEM, split operand (two 16-bit tiles per chunk): the epilogue stages
+// each chunk's operand values in shared memory and writes them with TMA bulk
+// stores, a group of four warps (one per TMEM lane quarter) per 16 replicas x
+// 128 spins tile: whole rows of the operand instead of one 64-byte fragment
+// per warp store (K2000 x 4096 FP16X2: 92.4 -> 90.0 ms per 2000 steps; the
+// one-tile FP16 operand measured slower, 63.0 -> 65.7 ms, and keeps plain stores).
+constexpr bool kTmaStore = true;
+constexpr uint32_t kStgBytes = 16 * 128 * 2;   // one staging tile [16 replicas][128 spins]
+
+__device__ __forceinline__ void sts_u16(uint32_t a, uint16_t v)
+{
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+}
 
 struct DenseMDArgs {
     float* phi;              // [Rpad][Npad] FP32 master
@@ -90,15 +114,17 @@ static __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p)
     return v;
 }
 
-template <int NH, int STAGES, int KSEG, bool FUSED, bool ONCHIP, bool F16, int KSUB, bool PHIT>
+template <int NH, int STAGES, int KSEG, bool FUSED, bool ONCHIP, bool F16, int KSUB, bool PHIT,
+          bool PAIR>
 __global__ void __launch_bounds__(kMDThreads, 1)
 k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmB,
-           const DenseMDArgs a)
+           const __grid_constant__ CUtensorMap tmS, const DenseMDArgs a)
 {
     // a ring stage holds KSUB consecutive 64-wide k-tiles: the KSUB J tiles,
     // then the KSUB phi tiles, then (FUSED, SHAREJ) the KSUB second phi tiles
     constexpr uint32_t A_BYTES = BM * BK * 2;
-    constexpr uint32_t B_BYTES = NH * BK * 2;
+    constexpr int NB = PAIR ? NH / 2 : NH;   // rows of a phi tile staged by this CTA
+    constexpr uint32_t B_BYTES = NB * BK * 2;
     // fused: one J tile per stage feeds the MMAs of both column halves.
     // SHAREJ (split phi against an exact J): one J tile per stage feeds the
     // MMAs of both K segments, phi_hi and phi_lo, into the same accumulator
@@ -112,14 +138,23 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
     static_assert(NH % 16 == 0 && NH <= 256, "UMMA N");
     static_assert(!ONCHIP || (NH <= 128 && !FUSED), "on-chip state: 4 NH TMEM columns");
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
-    static_assert((KSUB == 1 || KSUB == 2) && (KSUB == 1 || !FUSED), "k-tiles per stage");
+    static_assert((KSUB == 1 || KSUB == 2 || KSUB == 4) && (KSUB == 1 || !FUSED), "k-tiles per stage");
     static_assert(!PHIT || ONCHIP, "phi in TMEM is an on-chip state form");
+    static_assert(!PAIR || (PHIT && !FUSED), "pair form: phi in TMEM, separate halves");
+    // TS: operand values leave through shared-memory staging tiles and TMA
+    // stores (tmS: the operand buffers, box 128 spins x 16 replicas); NSEG
+    // distinct tiles per chunk (phi_hi, and phi_lo for split operands)
+    constexpr bool TS = PHIT && kTmaStore && KSEG != 1;
+    constexpr int NSEG = KSEG == 1 ? 1 : 2;
+    static_assert(B_BYTES % 1024 == 0 && 24 * STAGES + 48 <= 1024, "tile alignment, barrier block");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t bar = base + STAGES * STAGE_BYTES;
     const uint32_t full0 = bar, empty0 = bar + 8 * STAGES;
     const uint32_t accf0 = bar + 16 * STAGES, acce0 = accf0 + 16;
     const uint32_t tmem_slot = acce0 + 16;
+    const uint32_t done_bar = acce0 + 24;             // PAIR: the last MMA completed
+    const uint32_t pfull0 = bar + 16 * STAGES + 48;   // PAIR: the odd CTA's stage landed
     // ONCHIP: TMEM columns [2 NH, 4 NH) hold one state word of the tile's 2 NH
     // replicas: p, with phi in a shared-memory tile [2 NH columns][128 rows]
     // FP32 at phis; or (PHIT) phi, with p in global memory and the whole
@@ -128,6 +163,8 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.Mt, nc = blockIdx.x / a.Mt;
+    // PAIR: rank 0 (the even row tile) issues the MMAs; clusters are consecutive CTAs
+    const uint32_t crank = PAIR ? tc::cluster_rank() : 0u;
     const int m0 = mt * BM, n0 = nc * 2 * NH;
 
     if (threadIdx.x == 0) {
@@ -138,18 +175,30 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         }
         for (int hh = 0; hh < 2; ++hh) {
             tc::mbar_init(accf0 + 8 * hh, 1);
-            tc::mbar_init(acce0 + 8 * hh, kEpiWarps);
+            // PAIR: both CTAs' epilogue warps release the even CTA's accumulators
+            tc::mbar_init(acce0 + 8 * hh, PAIR ? 2 * kEpiWarps : kEpiWarps);
+        }
+        if constexpr (PAIR) {
+            tc::mbar_init(done_bar, 1);
+            for (int s = 0; s < STAGES; ++s) tc::mbar_init(pfull0 + 8 * s, 1);
         }
         tc::fence_mbar_init();
         tc::prefetch_tmap(&tmJ);
         tc::prefetch_tmap(&tmB);
+        if constexpr (TS) tc::prefetch_tmap(&tmS);
     }
     if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, TMEM_COLS);
-        tc::tmem_relinquish();
+        if constexpr (PAIR) {
+            tc::tmem_alloc2(tmem_slot, TMEM_COLS);
+            tc::tmem_relinquish2();
+        } else {
+            tc::tmem_alloc(tmem_slot, TMEM_COLS);
+            tc::tmem_relinquish();
+        }
     }
     tc::tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) tc::cluster_sync();   // the peer's barriers exist before any remote arrive
+    else __syncthreads();
     tc::tc_fence_after();
     uint32_t tmem;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(tmem) : "r"(tmem_slot));
@@ -187,7 +236,8 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                         if (*abort) break;
                         tc::fence_proxy_async_global();
                     }
-                    const int brow = (int)(m & 1) * a.Rpad + n0 + hh * NH;
+                    // PAIR: this CTA stages rows [NH/2 rank, +NH/2) of each phi tile
+                    const int brow = (int)(m & 1) * a.Rpad + n0 + hh * NH + (int)crank * NB;
                     // split operands: K runs over [hi | hi | lo] against
                     // [J_hi | J_lo | J_hi] (KSEG 3); with KSEG 2 a stage holds the
                     // J tile and the hi and lo tiles of the same k (columns kt and
@@ -195,9 +245,12 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     const int KTT = SHAREJ ? a.KT : KSEG * a.KT;   // a multiple of KSUB
                     for (int kt = 0; kt < KTT; kt += KSUB, ++it) {
                         const int s = it % STAGES;
-                        if (it >= STAGES &&
-                            !tc::mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort, kWaitNs))
-                            break;
+                        if (it >= STAGES) {
+                            const uint32_t ph = ((it / STAGES) - 1) & 1;   // PAIR: freed by the even CTA
+                            if (!(PAIR ? tc::mbar_wait_cl(empty0 + 8 * s, ph, abort, kWaitNs)
+                                       : tc::mbar_wait(empty0 + 8 * s, ph, abort, kWaitNs)))
+                                break;
+                        }
                         const uint32_t sa = base + s * STAGE_BYTES;
                         tc::mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
 #pragma unroll
@@ -222,22 +275,61 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     tc::mbar_wait(full0 + 8 * (k % STAGES), (k / STAGES) & 1, abort, 100000000ull);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && PAIR && crank != 0) {
+            // ---- PAIR, odd CTA: relay each landed stage to the MMA issuer ----
+            uint32_t it = 0;
+            const uint32_t peer_pfull0 = tc::mapa(pfull0, 0);
+            for (int64_t m = 0; m < a.S && !*abort; ++m)
+                for (int hh = 0; hh < NPASS && !*abort; ++hh) {
+                    const int KTT = SHAREJ ? a.KT : KSEG * a.KT;
+                    for (int kt = 0; kt < KTT; kt += KSUB, ++it) {
+                        const int s = it % STAGES;
+                        if (!tc::mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort, kWaitNs)) break;
+                        tc::mbar_arrive_remote(peer_pfull0 + 8 * s);
+                    }
+                }
+        } else if (lane == 0) {
             // ---- MMA issuer ----
-            constexpr uint32_t idesc = F16 ? tc::idesc_f16(BM, NH) : tc::idesc_bf16(BM, NH);
+            constexpr int MM = PAIR ? 2 * BM : BM;
+            constexpr uint32_t idesc = F16 ? tc::idesc_f16(MM, NH) : tc::idesc_bf16(MM, NH);
             uint32_t it = 0;
             for (int64_t m = 0; m < a.S && !*abort; ++m) {
                 for (int hh = 0; hh < NPASS && !*abort; ++hh) {
-                    if (m > 0 && !tc::mbar_wait(acce0 + 8 * hh, (uint32_t)((m - 1) & 1), abort, kWaitNs))
-                        break;
+                    if (m > 0) {
+                        const uint32_t ph = (uint32_t)((m - 1) & 1);
+                        if (!(PAIR ? tc::mbar_wait_cl(acce0 + 8 * hh, ph, abort, kWaitNs)
+                                   : tc::mbar_wait(acce0 + 8 * hh, ph, abort, kWaitNs)))
+                            break;
+                    }
                     tc::tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(hh * NH);
                     const int KTT = SHAREJ ? a.KT : KSEG * a.KT;
                     for (int kt = 0; kt < KTT; kt += KSUB, ++it) {
                         const int s = it % STAGES;
                         if (!tc::mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort, kWaitNs)) break;
+                        if (PAIR && !tc::mbar_wait_cl(pfull0 + 8 * s, (it / STAGES) & 1, abort, kWaitNs))
+                            break;
                         tc::tc_fence_after();
                         const uint32_t sa = base + s * STAGE_BYTES;
+                        if constexpr (PAIR) {
+#pragma unroll
+                            for (int u = 0; u < KSUB; ++u) {
+                                const uint64_t ad = tc::sdesc_k128(sa + u * A_BYTES);
+                                const uint64_t bd = tc::sdesc_k128(sa + KSUB * A_BYTES + u * B_BYTES);
+                                const bool first = (kt | u) == 0;
+#pragma unroll
+                                for (int kk = 0; kk < BK / 16; ++kk)
+                                    tc::mma2_f16(d, ad + 2 * kk, bd + 2 * kk, idesc, !(first && kk == 0));
+                                if constexpr (SHAREJ) {
+                                    const uint64_t bd1 = tc::sdesc_k128(sa + B2_OFF + u * B_BYTES);
+#pragma unroll
+                                    for (int kk = 0; kk < BK / 16; ++kk)
+                                        tc::mma2_f16(d, ad + 2 * kk, bd1 + 2 * kk, idesc, 1u);
+                                }
+                            }
+                            tc::mma_commit2(empty0 + 8 * s, 3);   // both CTAs' stage s is free
+                            continue;
+                        }
 #pragma unroll
                         for (int u = 0; u < KSUB; ++u) {
                             const uint64_t ad = tc::sdesc_k128(sa + u * A_BYTES);
@@ -262,8 +354,16 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                         }
                         tc::mma_commit(empty0 + 8 * s);
                     }
-                    tc::mma_commit(accf0 + 8 * hh);
+                    if constexpr (PAIR) tc::mma_commit2(accf0 + 8 * hh, 3);
+                    else tc::mma_commit(accf0 + 8 * hh);
                 }
+            }
+            if constexpr (PAIR) {
+                // every MMA issued (into both CTAs' TMEM, from both CTAs' shared
+                // memory) completes before either CTA frees them
+                volatile int no_abort = 0;   // waited for even after an abort
+                tc::mma_commit2(done_bar, 1);
+                tc::mbar_wait_cl(done_bar, 0, &no_abort, kWaitNs);
             }
         }
     } else {
@@ -278,6 +378,13 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         const int64_t win0 = a.S - (int64_t)a.W;
         const uint32_t tl = (uint32_t)(32 * quarter) << 16;   // this warp's TMEM lanes
         const uint32_t rloc = (uint32_t)(32 * quarter + lane);  // row within the tile
+        // PAIR, odd CTA: accumulators are released on the even CTA's barrier
+        const uint32_t acce_to = (PAIR && crank != 0) ? tc::mapa(acce0, 0) : acce0;
+        // TS: the four warps sharing csel (one per lane quarter) form a group with
+        // named barrier 2 + csel and staging tiles at stg; its first warp's lane 0
+        // issues the group's TMA stores
+        const uint32_t stg = bar + 1024 + (uint32_t)(csel * NSEG) * kStgBytes;
+        const bool gleader = (ew & 3) == 0 && lane == 0;
         if constexpr (ONCHIP) {
             // the tile's state moves on chip for the whole trajectory
             for (int hh = 0; hh < 2; ++hh)
@@ -322,8 +429,11 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                 const int pass = FUSED ? 0 : hh;
                 if (!FUSED || hh == 0) {
                     ok = __all_sync(0xffffffffu,
-                                    tc::mbar_wait(accf0 + 8 * pass, (uint32_t)(m & 1), abort, kWaitNs));
+                                    PAIR ? tc::mbar_wait_cl(accf0 + 8 * pass, (uint32_t)(m & 1), abort, kWaitNs)
+                                         : tc::mbar_wait(accf0 + 8 * pass, (uint32_t)(m & 1), abort, kWaitNs));
                     tc::tc_fence_after();
+                    // the group enters the chunk loop (and its barriers) together
+                    if constexpr (TS) ok = tc::named_bar_and(2 + csel, 128, ok);
                 }
                 if (ok && PHIT) {
                     // phi in TMEM next to the accumulators, p in global memory
@@ -341,6 +451,12 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                             for (int j = 0; j < 16; ++j)
                                 npp[j] = a.p[(size_t)(n0 + col + 16 * kCS + j) * a.Npad + row];
                         }
+                        if constexpr (TS) {
+                            // the group's staging tiles are free once the stores of
+                            // its previous chunk have read them
+                            if (gleader) tc::bulk_wait_read0();
+                            tc::named_bar(2 + csel, 128);
+                        }
                         tc::tmem_wait_ld();
                         if (row_ok) {
 #pragma unroll
@@ -349,27 +465,55 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                 const float f = __uint_as_float(fv[j]);
                                 const float L = __uint_as_float(v[j]) * a.lscale + hr * fabsf(f);
                                 const float phi2 = f * f;
-                                float pw = f;
-                                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                                const float pw = pot_pow(f, phi2, mhalf);
                                 const float pn = pp[j] - fmaf(cf.x, pw, cf.y * L);
                                 const float fn = fmaf(cf.z, pn, f);
                                 a.p[o] = pn;
                                 fv[j] = __float_as_uint(fn);
-                                const size_t ob = (size_t)(n0 + col + j) * Kb + row;
                                 const float fs = fn * a.oscale;
                                 const uint16_t hi = cvt16<F16>(fs);
-                                nb[ob] = hi;
-                                if (KSEG == 2) nb[ob + a.Npad] = cvt16<F16>(fs - from16<F16>(hi));
-                                if (KSEG == 3) {
-                                    nb[ob + a.Npad] = hi;
-                                    nb[ob + 2 * a.Npad] = cvt16<F16>(fs - from16<F16>(hi));
+                                if constexpr (TS) {
+                                    const uint32_t sb = stg + (uint32_t)(j * 128) * 2u + rloc * 2u;
+                                    sts_u16(sb, hi);
+                                    if constexpr (KSEG != 1)
+                                        sts_u16(sb + kStgBytes, cvt16<F16>(fs - from16<F16>(hi)));
+                                } else {
+                                    const size_t ob = (size_t)(n0 + col + j) * Kb + row;
+                                    nb[ob] = hi;
+                                    if (KSEG == 2) nb[ob + a.Npad] = cvt16<F16>(fs - from16<F16>(hi));
+                                    if (KSEG == 3) {
+                                        nb[ob + a.Npad] = hi;
+                                        nb[ob + 2 * a.Npad] = cvt16<F16>(fs - from16<F16>(hi));
+                                    }
                                 }
                                 if (in_win) a.w[o] += fn;
+                            }
+                        } else if constexpr (TS) {
+                            // spin rows beyond N keep a zero operand
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const uint32_t sb = stg + (uint32_t)(j * 128) * 2u + rloc * 2u;
+                                sts_u16(sb, 0);
+                                if constexpr (KSEG != 1) sts_u16(sb + kStgBytes, 0);
                             }
                         }
                         // .sync.aligned: every lane of the warp, outside the row_ok branch
                         tc::tmem_st16(tmem + tl + (uint32_t)(2 * NH + col), fv);
                         tc::tmem_wait_st();
+                        if constexpr (TS) {
+                            tc::fence_proxy_async_smem();
+                            tc::named_bar(2 + csel, 128);
+                            if (gleader) {
+                                const int y = (int)((m + 1) & 1) * a.Rpad + n0 + col;
+                                tc::tma_store_2d(&tmS, m0, y, stg);
+                                if (KSEG == 2) tc::tma_store_2d(&tmS, a.Npad + m0, y, stg + kStgBytes);
+                                if (KSEG == 3) {
+                                    tc::tma_store_2d(&tmS, a.Npad + m0, y, stg);
+                                    tc::tma_store_2d(&tmS, 2 * a.Npad + m0, y, stg + kStgBytes);
+                                }
+                                tc::bulk_commit();
+                            }
+                        }
                         if (more) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) pp[j] = npp[j];
@@ -377,7 +521,10 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     }
                     tc::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(acce0 + 8 * pass);
+                    if (lane == 0) {
+                        if (PAIR && crank != 0) tc::mbar_arrive_remote(acce_to + 8 * pass);
+                        else tc::mbar_arrive(acce0 + 8 * pass);
+                    }
                 } else if (ok && ONCHIP) {
 #pragma unroll 1
                     for (int c = csel; c < NH / 16; c += kCS) {
@@ -396,8 +543,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                             for (int j = 0; j < 16; ++j) {
                                 const float L = __uint_as_float(v[j]) * a.lscale + hr * fabsf(phl[j]);
                                 const float phi2 = phl[j] * phl[j];
-                                float pw = phl[j];
-                                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                                const float pw = pot_pow(phl[j], phi2, mhalf);
                                 const float pn = __uint_as_float(pv[j]) - fmaf(cf.x, pw, cf.y * L);
                                 const float fn = fmaf(cf.z, pn, phl[j]);
                                 pv[j] = __float_as_uint(pn);
@@ -447,8 +593,7 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                                 const size_t o = (size_t)(rbase + j) * a.Npad + row;
                                 const float L = __uint_as_float(v[j]) * a.lscale + hr * fabsf(ph[j]);
                                 const float phi2 = ph[j] * ph[j];
-                                float pw = ph[j];
-                                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                                const float pw = pot_pow(ph[j], phi2, mhalf);
                                 const float pn = pp[j] - fmaf(cf.x, pw, cf.y * L);
                                 const float fn = fmaf(cf.z, pn, ph[j]);
                                 a.p[o] = pn;
@@ -481,6 +626,10 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                     }
                 }
                 if (FUSED && hh == 0) continue;
+                // TS: this half's operand stores complete in global memory
+                if constexpr (TS) {
+                    if (gleader) tc::bulk_wait0();
+                }
                 // Phi^(m+1) of this half -> visible to the other CTAs' TMA loads
                 tc::fence_proxy_async_global();
                 // all epilogue warps meet here every half-step; the barrier also
@@ -524,11 +673,16 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
         }
     }
     tc::tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    // PAIR: neither CTA frees its shared memory or TMEM while the pair's MMAs
+    // or remote arrives may still touch them
+    if constexpr (PAIR) tc::cluster_sync();
+    else __syncthreads();
     if (*abort && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_TIMEOUT);
     if (warp == 1) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, TMEM_COLS);
+        if constexpr (PAIR) tc::tmem_dealloc2(tmem, TMEM_COLS);
+        else tc::tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 
@@ -604,13 +758,23 @@ static __global__ void k_dense_out(DenseMDArgs a, float inv_w, float* phi_out, f
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, HQA_DEV_NONFINITE);
 }
 
-template <int NH, int STAGES, bool TWOB, bool ONCHIP, int KSUB, bool PHIT>
+// Shared memory after the barrier block: the phi tile (on chip, not PHIT) or
+// the epilogue's operand staging tiles (PHIT with TMA stores).
+constexpr int md_tail(int nh, int kseg, bool onchip, bool phit)
+{
+    return onchip && !phit ? 2 * nh * BM * 4
+         : phit && kTmaStore && kseg != 1 ? kCS * 2 * (int)kStgBytes
+                             : 0;
+}
+
+template <int NH, int STAGES, bool TWOB, int KSUB, bool PAIR, int TAIL>
 size_t md_smem()
 {
     // alignment slack, ring (KSUB J tiles and KSUB or 2 KSUB phi tiles per
-    // stage), barrier block (1 KB), shared-memory phi tile (on chip, not PHIT)
-    return 1024 + (size_t)STAGES * KSUB * (BM * BK * 2 + (TWOB ? 2 : 1) * NH * BK * 2) + 1024 +
-           (ONCHIP && !PHIT ? (size_t)2 * NH * BM * 4 : 0);
+    // stage, a pair's CTA staging half of each phi tile), barrier block
+    // (1 KB), tail
+    constexpr int NB = PAIR ? NH / 2 : NH;
+    return 1024 + (size_t)STAGES * KSUB * (BM * BK * 2 + (TWOB ? 2 : 1) * NB * BK * 2) + 1024 + TAIL;
 }
 
 // The tile's state (phi, p) stays on chip for the whole trajectory when its
@@ -630,10 +794,10 @@ constexpr bool kFusedHalves = false;
 // Deeper rings measured no faster on K2000 x 4096: with the state in global
 // memory instead (freeing the 128 KB phi tile), 4 and 7 stages ran FP16X2 in
 // 115.5 ms per 2000 steps against 114.2 on chip, FP16 in 84.3 and 87.6 against 77.8.
-constexpr int md_stages(int nh, bool twob, bool onchip, int ksub, bool phit)
+constexpr int md_stages(int nh, bool twob, int tail, int ksub, bool phit, bool pair)
 {
-    const int stage = ksub * (BM * BK * 2 + (twob ? 2 : 1) * nh * BK * 2);
-    const int n = (227 * 1024 - 2048 - 64 - (onchip && !phit ? 2 * nh * BM * 4 : 0)) / stage;
+    const int stage = ksub * (BM * BK * 2 + (twob ? 2 : 1) * (pair ? nh / 2 : nh) * BK * 2);
+    const int n = (227 * 1024 - 2048 - 64 - tail) / stage;
     const int cap = phit ? 8 : 4;
     return n > cap ? cap : n;
 }
@@ -647,11 +811,23 @@ constexpr int md_stages(int nh, bool twob, bool onchip, int ksub, bool phit)
 // stages of one k-tile) -> 105.8 ms (2 stages of two), FP16 78.0 -> 84.0 ->
 // 69.3 ms, all bitwise identical.
 constexpr bool kPhiInTmem = true;
-constexpr int kKSub = 2;
+constexpr int kKSub = 4;
 
-constexpr int md_ksub(int nh, bool twob, bool onchip, bool phit)
+constexpr int md_ksub(int nh, bool twob, int tail, bool phit, bool pair)
 {
-    return kKSub > 1 && phit && md_stages(nh, twob, onchip, 2, phit) >= 2 ? 2 : 1;
+    // 4 only for pairs: their row tiles pair up, so Npad is a multiple of 256
+    return kKSub >= 4 && phit && pair && md_stages(nh, twob, tail, 4, phit, pair) >= 2 ? 4
+         : kKSub >= 2 && phit && md_stages(nh, twob, tail, 2, phit, pair) >= 2      ? 2
+                                                                                   : 1;
+}
+
+// CTA pairs (one cta_group::2 MMA per K slice for two row tiles) wherever phi
+// is in TMEM and the row tiles pair up.
+constexpr bool kPairMMA = true;
+
+inline bool use_pair(int nh, int Mt)
+{
+    return kPairMMA && kPhiInTmem && !kFusedHalves && onchip_ok(nh) && Mt % 2 == 0;
 }
 
 // Column halves: NH replicas (multiple of 16, <= 256); Nc = ceil(R / 2NH) with
@@ -674,37 +850,60 @@ inline int pick_nh(int Mt, int R, int sms)
     return best;
 }
 
-template <int NH, int KSEG, bool F16>
-hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
-                             const CUtensorMap& tmA, const CUtensorMap& tmB)
+template <int NH, int KSEG, bool F16, bool PAIR>
+hqa_status launch_dense_md_p(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
+                             const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmS)
 {
     constexpr bool ONCHIP = onchip_ok(NH) && !kFusedHalves;
     constexpr bool TWOB = kFusedHalves || KSEG == 2;   // two phi tiles per ring stage
     constexpr bool PHIT = ONCHIP && kPhiInTmem;
-    constexpr int KSUB = kFusedHalves ? 1 : md_ksub(NH, TWOB, ONCHIP, PHIT);
-    constexpr int STAGES = md_stages(NH, TWOB, ONCHIP, KSUB, PHIT);
+    constexpr int TAIL = md_tail(NH, KSEG, ONCHIP, PHIT);
+    constexpr int KSUB = kFusedHalves ? 1 : md_ksub(NH, TWOB, TAIL, PHIT, PAIR);
+    constexpr int STAGES = md_stages(NH, TWOB, TAIL, KSUB, PHIT, PAIR);
     static_assert(STAGES >= 2, "ring depth");
-    const size_t smem = md_smem<NH, STAGES, TWOB, ONCHIP, KSUB, PHIT>();
+    const size_t smem = md_smem<NH, STAGES, TWOB, KSUB, PAIR, TAIL>();
     if (smem > ctx->smem_optin) return HQA_ERR_TOO_LARGE;
     if (a.KT % KSUB != 0) return HQA_ERR_INVALID_ARG;   // Npad is a multiple of 128
-    const void* fn = (const void*)k_dense_md<NH, STAGES, KSEG, kFusedHalves, ONCHIP, F16, KSUB, PHIT>;
+    if (PAIR && (grid % 2 != 0 || a.Mt % 2 != 0)) return HQA_ERR_INVALID_ARG;
+    const void* fn =
+        (const void*)k_dense_md<NH, STAGES, KSEG, kFusedHalves, ONCHIP, F16, KSUB, PHIT, PAIR>;
     if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
     void* args[] = {const_cast<CUtensorMap*>(&tmA), const_cast<CUtensorMap*>(&tmB),
-                    const_cast<DenseMDArgs*>(&a)};
+                    const_cast<CUtensorMap*>(&tmS), const_cast<DenseMDArgs*>(&a)};
     // a cooperative launch (every CTA co-resident: the column-group counters are
     // waited on across CTAs), issued through the launch-attribute form so that
     // a stream capture records it as a cooperative kernel node
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;   // PAIR: row tiles 2t, 2t+1
+    attr[1].val.clusterDim.x = 2;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kMDThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = PAIR ? 2 : 1;
     cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+    if (PAIR && e == cudaErrorCooperativeLaunchTooLarge && !hqa_capturing()) {
+        // a profiler replaying kernels refuses the cooperative form of a cluster
+        // launch.  Every wait in the kernel is bounded, so the plain cluster
+        // launch is safe when the clusters fit: CTAs that were not all resident
+        // would end in HQA_DEV_TIMEOUT, not hang
+        (void)cudaGetLastError();
+        cfg.attrs = attr + 1;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) == cudaSuccess && ncl >= grid / 2) {
+            e = cudaLaunchKernelExC(&cfg, fn, args);
+        } else {
+            (void)cudaGetLastError();
+            e = cudaErrorCooperativeLaunchTooLarge;
+        }
+    }
     if (e == cudaErrorCooperativeLaunchTooLarge) {
         (void)cudaGetLastError();
         return HQA_ERR_TOO_LARGE;
@@ -716,17 +915,28 @@ hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaS
     return HQA_OK;
 }
 
+template <int NH, int KSEG, bool F16>
+hqa_status launch_dense_md_t(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaStream_t st,
+                             const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmS)
+{
+    if constexpr (onchip_ok(NH) && !kFusedHalves && kPhiInTmem) {
+        if (use_pair(NH, a.Mt))
+            return launch_dense_md_p<NH, KSEG, F16, true>(ctx, a, grid, st, tmA, tmB, tmS);
+    }
+    return launch_dense_md_p<NH, KSEG, F16, false>(ctx, a, grid, st, tmA, tmB, tmS);
+}
 
 // Launches the persistent kernel for column width NH and K segments kseg.
 template <bool F16>
 hqa_status dense_md_dispatch(hqa_ctx* ctx, const DenseMDArgs& a, int NH, int kseg, int grid,
-                             cudaStream_t st, const CUtensorMap& tmA, const CUtensorMap& tmB)
+                             cudaStream_t st, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                             const CUtensorMap& tmS)
 {
 #define HQA_NH_CASE(V)                                                                        \
     case V:                                                                                    \
-        return kseg == 3 ? launch_dense_md_t<V, 3, F16>(ctx, a, grid, st, tmA, tmB)            \
-             : kseg == 2 ? launch_dense_md_t<V, 2, F16>(ctx, a, grid, st, tmA, tmB)            \
-                         : launch_dense_md_t<V, 1, F16>(ctx, a, grid, st, tmA, tmB);
+        return kseg == 3 ? launch_dense_md_t<V, 3, F16>(ctx, a, grid, st, tmA, tmB, tmS)            \
+             : kseg == 2 ? launch_dense_md_t<V, 2, F16>(ctx, a, grid, st, tmA, tmB, tmS)            \
+                         : launch_dense_md_t<V, 1, F16>(ctx, a, grid, st, tmA, tmB, tmS);
     switch (NH) {
         HQA_NH_CASE(256)
         HQA_NH_CASE(240)
@@ -745,9 +955,9 @@ hqa_status dense_md_dispatch(hqa_ctx* ctx, const DenseMDArgs& a, int NH, int kse
 
 extern template hqa_status dense_md_dispatch<false>(hqa_ctx*, const DenseMDArgs&, int, int, int,
                                                     cudaStream_t, const CUtensorMap&,
-                                                    const CUtensorMap&);
+                                                    const CUtensorMap&, const CUtensorMap&);
 extern template hqa_status dense_md_dispatch<true>(hqa_ctx*, const DenseMDArgs&, int, int, int,
                                                    cudaStream_t, const CUtensorMap&,
-                                                   const CUtensorMap&);
+                                                   const CUtensorMap&, const CUtensorMap&);
 
 }  // namespace hqa_dense

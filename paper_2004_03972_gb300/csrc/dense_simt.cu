@@ -124,8 +124,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dense_simt(const SimtArgs a)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const float phi2 = phv[j] * phv[j];
-                        float pw = phv[j];
-                        for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                        const float pw = pot_pow(phv[j], phi2, mhalf);
                         pn[j] = ppv[j] - fmaf(cf.x, pw, cf.y * Lv[j]);
                         fn[j] = fmaf(cf.z, pn[j], phv[j]);
                     }

@@ -28,6 +28,23 @@ enum : uint32_t {
         }                                                    \
     } while (0)
 
+// The potential's force term phi^(M-1) = phi (phi^2)^((M-2)/2), for the even
+// M in [2, 12] that hqa_create_schedule accepts: at most kMaxMHalf squarings,
+// written as a fixed sequence of predicated multiplications.  A loop with a
+// data-dependent trip count inside an unrolled per-element update keeps the
+// compiler from interleaving the independent elements; this form performs
+// the same multiplications in the same order (bitwise identical results).
+constexpr int kMaxMHalf = 5;
+
+__device__ __forceinline__ float pot_pow(float phi, float phi2, int mhalf)
+{
+    float pw = phi;
+#pragma unroll
+    for (int q = 0; q < kMaxMHalf; ++q)
+        if (q < mhalf) pw = __fmul_rn(pw, phi2);
+    return pw;
+}
+
 // One step of the kick/drift coefficient table (see hqa_run).
 struct StepCoef {
     float kA;  // c_j h alpha(j dt) M       multiplies phi^(M-1)

@@ -205,8 +205,7 @@ __device__ __forceinline__ void md_block(const MDArgs& a, int blk, int gslot)
             float L = L0;
             if (a.h) L += 2.f * __ldg(a.h + row) * fabsf(phi);
             const float phi2 = phi * phi;
-            float pw = phi;
-            for (int q = 0; q < mhalf; ++q) pw *= phi2;
+            const float pw = pot_pow(phi, phi2, mhalf);
             float p = a.state_in_smem ? lds_f32(sp + e * 4u) : gp[e];
             p = p - fmaf(cf.x, pw, cf.y * L);
             const float phin = fmaf(cf.z, p, phi);

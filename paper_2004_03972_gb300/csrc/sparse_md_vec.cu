@@ -345,8 +345,7 @@ __global__ void __launch_bounds__(REG > 0 ? reg_threads(REG, BF16) : kMaxThreads
                 for (int u = 0; u < V; ++u) {
                     const float L = Lsum[u] + rhr[kk] * fabsf(rphi[kk][u]);
                     const float phi2 = rphi[kk][u] * rphi[kk][u];
-                    float pw = rphi[kk][u];
-                    for (int m = 0; m < mhalf; ++m) pw *= phi2;
+                    const float pw = pot_pow(rphi[kk][u], phi2, mhalf);
                     rp[kk][u] = rp[kk][u] - fmaf(cf.x, pw, cf.y * L);
                     rphi[kk][u] = fmaf(cf.z, rp[kk][u], rphi[kk][u]);
                 }
@@ -439,8 +438,7 @@ __global__ void __launch_bounds__(REG > 0 ? reg_threads(REG, BF16) : kMaxThreads
             for (int u = 0; u < V; ++u) {
                 const float L = Lsum[u] + hr * fabsf(phi[u]);
                 const float phi2 = phi[u] * phi[u];
-                float pw = phi[u];
-                for (int m = 0; m < mhalf; ++m) pw *= phi2;
+                const float pw = pot_pow(phi[u], phi2, mhalf);
                 p[u] = p[u] - fmaf(cf.x, pw, cf.y * L);
                 phi[u] = fmaf(cf.z, p[u], phi[u]);
             }

@@ -196,8 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_sparse_stream(const StreamArgs a)
             for (int e = 0; e < V; ++e) {
                 const float Le = hr != 0.f ? L[e] + hr * fabsf(ph[e]) : L[e];
                 const float phi2 = ph[e] * ph[e];
-                float pw = ph[e];
-                for (int q = 0; q < mhalf; ++q) pw *= phi2;
+                const float pw = pot_pow(ph[e], phi2, mhalf);
                 pp[e] = pp[e] - fmaf(cf.x, pw, cf.y * Le);
                 fn[e] = fmaf(cf.z, pp[e], ph[e]);
             }
