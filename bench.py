@@ -315,7 +315,7 @@ def kernel_name(hqa, plan, prec_name):
             return "k_dense_simt<1>"
         kseg = 2 if prec_name.endswith("X2") else 1
         f16 = "true" if prec_name.startswith("PREC_FP16") else "false"
-        return f"k_dense_md<{plan['replicas_per_block'] // 2},*,{kseg},*,*,{f16}>"
+        return f"k_dense_md<{plan['replicas_per_block'] // 2},*,{kseg},*,*,{f16},*,*,*>"
     if k == hqa.KERNEL_STREAM:
         return f"k_sparse_stream<{'true' if prec_name == 'PREC_BF16' else 'false'}>"
     base = "k_sparse_md_vec" if k == hqa.KERNEL_VECTOR else "k_sparse_md"

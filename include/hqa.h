@@ -510,8 +510,9 @@ hqa_status hqa_autotune(hqa_ctx* ctx, const hqa_schedule* sched, int32_t replica
  * already prepared by an identical earlier call without capture: launch
  * plans, the schedule table, workspaces and batch work tables.  A call that
  * would have to allocate, upload from the host or synchronise returns
- * HQA_ERR_UNSUPPORTED instead (the dense tensor-core MD, a cooperative launch,
- * is recorded as a cooperative kernel node);
+ * HQA_ERR_UNSUPPORTED instead (the dense tensor-core MD is recorded as a
+ * cooperative kernel node, or as a kernel node with a 2-CTA cluster shape
+ * when its row tiles run as CTA pairs);
  * hqa_capture_end then returns the first failure of the capture and no
  * graph.  hqa_capture_end must follow every successful hqa_capture_begin.
  * The graph replays the same launches with the same pointers and

@@ -870,40 +870,40 @@ hqa_status launch_dense_md_p(hqa_ctx* ctx, const DenseMDArgs& a, int grid, cudaS
     if (hqa_smem_attr(fn, smem) != cudaSuccess) return HQA_ERR_CUDA;
     void* args[] = {const_cast<CUtensorMap*>(&tmA), const_cast<CUtensorMap*>(&tmB),
                     const_cast<CUtensorMap*>(&tmS), const_cast<DenseMDArgs*>(&a)};
-    // a cooperative launch (every CTA co-resident: the column-group counters are
-    // waited on across CTAs), issued through the launch-attribute form so that
-    // a stream capture records it as a cooperative kernel node
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    attr[1].id = cudaLaunchAttributeClusterDimension;   // PAIR: row tiles 2t, 2t+1
-    attr[1].val.clusterDim.x = 2;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
+    // every CTA must be co-resident: the column-group counters are waited on
+    // across CTAs.  One-CTA form: a cooperative launch, issued through the
+    // launch-attribute form so that a stream capture records it as a
+    // cooperative kernel node.  PAIR: a cluster launch (2 CTAs per cluster)
+    // after checking that all clusters fit at once; the cooperative form of a
+    // cluster launch is refused under the profiler.  Every wait in the kernel
+    // is bounded, so a grid that were not all resident would end in
+    // HQA_DEV_TIMEOUT, not hang.
+    cudaLaunchAttribute attr[1];
+    if constexpr (PAIR) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;   // row tiles 2t, 2t+1
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kMDThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = PAIR ? 2 : 1;
-    cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
-    if (PAIR && e == cudaErrorCooperativeLaunchTooLarge && !hqa_capturing()) {
-        // a profiler replaying kernels refuses the cooperative form of a cluster
-        // launch.  Every wait in the kernel is bounded, so the plain cluster
-        // launch is safe when the clusters fit: CTAs that were not all resident
-        // would end in HQA_DEV_TIMEOUT, not hang
-        (void)cudaGetLastError();
-        cfg.attrs = attr + 1;
-        cfg.numAttrs = 1;
+    cfg.numAttrs = 1;
+    if constexpr (PAIR) {
         int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) == cudaSuccess && ncl >= grid / 2) {
-            e = cudaLaunchKernelExC(&cfg, fn, args);
-        } else {
+        if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess) {
             (void)cudaGetLastError();
-            e = cudaErrorCooperativeLaunchTooLarge;
+            return HQA_ERR_CUDA;
         }
+        if (ncl < grid / 2) return HQA_ERR_TOO_LARGE;
     }
+    cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
         (void)cudaGetLastError();
         return HQA_ERR_TOO_LARGE;
