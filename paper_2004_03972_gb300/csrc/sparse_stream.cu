@@ -30,6 +30,7 @@
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kGatherBatch = 4;   // neighbour gathers issued together
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s bound on the grid barrier
 
 struct StreamArgs {
@@ -145,7 +146,24 @@ __device__ __forceinline__ void cell_field(const StreamArgs& a, const void* op, 
 #pragma unroll
     for (int e = 0; e < V; ++e) L[e] = 0.f;
     const int k0 = __ldg(a.row_ptr + i), k1 = __ldg(a.row_ptr + i + 1);
-    for (int k = k0; k < k1; ++k) {
+    int k = k0;
+    // four neighbours' gathers in flight at once (the same accumulation order)
+    for (; k + kGatherBatch <= k1; k += kGatherBatch) {
+        int j[kGatherBatch];
+        float s[kGatherBatch], x[kGatherBatch][V];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            j[u] = __ldg(a.col + k + u);
+            s[u] = (float)__ldg(a.val + k + u);
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) Vec<BF16>::load(op, (size_t)j[u] * a.Rpad + c, x[u]);
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u)
+#pragma unroll
+            for (int e = 0; e < V; ++e) L[e] = fmaf(s[u], x[u][e], L[e]);
+    }
+    for (; k < k1; ++k) {
         const int j = __ldg(a.col + k);
         const float s = (float)__ldg(a.val + k);
         float x[V];
