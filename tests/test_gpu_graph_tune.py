@@ -113,11 +113,13 @@ def test_unprepared_capture_fails_cleanly(hqa):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 3, 4])
-def test_dense_md_graph_replay(hqa, prec):
-    """The dense MD (the persistent tcgen05 kernel, recorded as a cooperative kernel
-    node, or the per-step FP32 CUDA-core launches) replays from a graph with the
-    results of an eager run, bitwise."""
-    inst = instances.sk_pm1(256, 7)
+@pytest.mark.parametrize("n", [256, 300])
+def test_dense_md_graph_replay(hqa, prec, n):
+    """The dense MD replays from a graph with the results of an eager run, bitwise:
+    the persistent tcgen05 kernel as a 2-CTA cluster node (N = 256: two row tiles,
+    one CTA pair) or as a cooperative kernel node (N = 300: three row tiles, one
+    CTA each), and the per-step FP32 CUDA-core launches."""
+    inst = instances.sk_pm1(n, 7)
     ctx = hqa.Context.from_instance(inst)
     R, S = 128, 50
     st = torch.cuda.Stream()

@@ -19,8 +19,9 @@ def hqa():
     return H
 
 
-def test_unset_flag_times_out_and_context_recovers(hqa):
-    inst = instances.sk_pm1(256, 17)
+@pytest.mark.parametrize("n", [256, 300])   # a CTA pair (two row tiles) / one CTA per row tile
+def test_unset_flag_times_out_and_context_recovers(hqa, n):
+    inst = instances.sk_pm1(n, 17)
     ctx = hqa.Context.from_instance(inst)
     R, S = 128, 60
     flag = torch.zeros(1, dtype=torch.int32, device="cuda")
