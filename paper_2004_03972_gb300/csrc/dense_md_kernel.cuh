@@ -86,6 +86,45 @@ __device__ __forceinline__ void sts_u16(uint32_t a, uint16_t v)
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
 }
 
+// Split-operand epilogue arithmetic on pairs of elements (Blackwell's packed
+// FP32 add/mul/fma, each lane of a pair rounded as the scalar operation).
+constexpr bool kPackedEpilogue = true;
+
+__device__ __forceinline__ uint64_t pk2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo2(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi2(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// a - b as a + (-b): the same IEEE result
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) { return add2(a, b ^ 0x8000000080000000ull); }
+
+template <bool F16>
+__device__ __forceinline__ uint32_t cvt16x2(float lo, float hi)   // lo -> bits 0-15
+{
+    return (uint32_t)cvt16<F16>(lo) | ((uint32_t)cvt16<F16>(hi) << 16);
+}
+
 struct DenseMDArgs {
     float* phi;              // [Rpad][Npad] FP32 master
     float* p;                // [Rpad][Npad]
@@ -458,7 +497,47 @@ k_dense_md(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUte
                             tc::named_bar(2 + csel, 128);
                         }
                         tc::tmem_wait_ld();
-                        if (row_ok) {
+                        if (TS && kPackedEpilogue && row_ok) {
+                            // pairs of replica columns: L = hr |phi| + acc lscale (fused),
+                            // then the kick, drift, split and stores as below
+                            const uint64_t ls2 = pk2(a.lscale, a.lscale), hr2 = pk2(hr, hr);
+                            const uint64_t cx2 = pk2(cf.x, cf.x), cy2 = pk2(cf.y, cf.y);
+                            const uint64_t cz2 = pk2(cf.z, cf.z), os2 = pk2(a.oscale, a.oscale);
+#pragma unroll
+                            for (int j = 0; j < 16; j += 2) {
+                                const size_t o0 = (size_t)(n0 + col + j) * a.Npad + row;
+                                const size_t o1 = o0 + a.Npad;
+                                const uint64_t f2 = pk2(__uint_as_float(fv[j]), __uint_as_float(fv[j + 1]));
+                                const uint64_t af2 = f2 & 0x7fffffff7fffffffull;   // |phi|
+                                const uint64_t L2 = fma2(hr2, af2, mul2(pk2(__uint_as_float(v[j]),
+                                                                            __uint_as_float(v[j + 1])), ls2));
+                                const uint64_t sq2 = mul2(f2, f2);
+                                uint64_t pw2 = f2;
+#pragma unroll
+                                for (int q = 0; q < kMaxMHalf; ++q)
+                                    if (q < mhalf) pw2 = mul2(pw2, sq2);
+                                const uint64_t pn2 = sub2(pk2(pp[j], pp[j + 1]), fma2(cx2, pw2, mul2(cy2, L2)));
+                                const uint64_t fn2 = fma2(cz2, pn2, f2);
+                                a.p[o0] = lo2(pn2);
+                                a.p[o1] = hi2(pn2);
+                                fv[j] = __float_as_uint(lo2(fn2));
+                                fv[j + 1] = __float_as_uint(hi2(fn2));
+                                const uint64_t fs2 = mul2(fn2, os2);
+                                const uint32_t h2 = cvt16x2<F16>(lo2(fs2), hi2(fs2));
+                                const uint64_t r2 = sub2(fs2, pk2(from16<F16>((uint16_t)h2),
+                                                                  from16<F16>((uint16_t)(h2 >> 16))));
+                                const uint32_t l2 = cvt16x2<F16>(lo2(r2), hi2(r2));
+                                const uint32_t sb = stg + (uint32_t)(j * 128) * 2u + rloc * 2u;
+                                sts_u16(sb, (uint16_t)h2);
+                                sts_u16(sb + 256u, (uint16_t)(h2 >> 16));
+                                sts_u16(sb + kStgBytes, (uint16_t)l2);
+                                sts_u16(sb + kStgBytes + 256u, (uint16_t)(l2 >> 16));
+                                if (in_win) {
+                                    a.w[o0] += lo2(fn2);
+                                    a.w[o1] += hi2(fn2);
+                                }
+                            }
+                        } else if (row_ok) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const size_t o = (size_t)(n0 + col + j) * a.Npad + row;
